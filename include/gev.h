@@ -1,0 +1,128 @@
+/*
+ * gev.h -- C ABI of the GB300 dense generalized Hermitian eigensolver.
+ *
+ * Problem (Eq. 2): H C = S C Lambda with H Hermitian and S Hermitian positive definite, N x N,
+ * real FP64 or complex128.  The k lowest eigenpairs are returned.  The path follows the reduction
+ * of the section "Current Status of the Implementation" (steps 1-3 and the back-transformation
+ * C = U^{-1} C~; Table 1 names the steps Choles., Invert, Multiply, Tridiag., Solve, Back, Mult.):
+ *
+ *   1  Cholesky          S = L L^H                      (L = U^H; the paper writes S = U^T U)
+ *   2  Invert            X = L^{-1}                      (kept resident for SCF reuse)
+ *   3  Multiply          A = X H X^H
+ *   4a full -> band      A = Q1 B Q1^H   (two-stage tridiagonalisation, "ELPA2")
+ *   4b band -> tridiag   B = Q2 T Q2^H   (bulge chasing; T real symmetric)
+ *   5  Solve             T = Z Lambda Z^T by divide and conquer
+ *   6  Back              Y = Q1 Q2 Z
+ *   7  Mult.             C = X^H Y
+ *
+ * Conventions shared by every entry point:
+ *   - Matrices are column-major DEVICE pointers with a leading dimension ld >= max(1, n).  Complex
+ *     data are interleaved (re, im) doubles (the layout of C99 double complex / complex128).
+ *   - Only the lower triangle of H and S is read; the caller's H and S are never written.
+ *   - The caller owns H, S, the eigenvalue array and C.  The handle owns its workspace and the
+ *     resident factor X = L^{-1}.
+ *   - All work is issued on the stream given in gev_opts (0 = legacy default stream) of the device
+ *     given there.  Entry points that return results synchronise that stream before returning.
+ *   - Eigenvalues ascend.  C is S-orthonormal (C^H S C = I).  In each column the entry of largest
+ *     modulus (first index on exact ties) is real and positive.
+ *   - Return value 0 = success, -i = the i-th argument is invalid (nothing was launched), or one of
+ *     the positive GEV_ERR_* codes below.  After an error the outputs are unspecified, but the handle
+ *     stays usable; GEV_ERR_CUDA means the CUDA context itself reported an error.
+ */
+#ifndef GEV_H
+#define GEV_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gev_sys gev_sys; /* opaque, one per system (k-point / spin channel) */
+
+typedef enum { GEV_F64 = 0, GEV_C128 = 1 } gev_dtype;
+typedef enum { GEV_PLAIN = 0, GEV_MIXED = 1 } gev_precision;
+
+enum {
+  GEV_OK = 0,
+  GEV_ERR_NOT_SPD = 1,               /* S not positive definite; report.info = pivot index + 1 */
+  GEV_ERR_NO_CONVERGENCE = 2,        /* an iteration cap was hit (secular roots, refinement) */
+  GEV_ERR_TIMEOUT = 3,               /* a bounded device wait gave up; the kernel returned */
+  GEV_ERR_OOM = 4,                   /* workspace allocation failed or exceeds workspace_limit */
+  GEV_ERR_CUDA = 5,                  /* a CUDA runtime call failed */
+  GEV_ERR_REUSE_WITHOUT_FACTOR = 6,  /* S == NULL but no resident factor is held */
+  GEV_ERR_UNSUPPORTED = 7            /* option combination not available */
+};
+
+/* Steps timed in gev_report.ms (milliseconds, CUDA events on the solve stream). */
+enum {
+  GEV_STEP_CHOLESKY = 0,
+  GEV_STEP_INVERT = 1,
+  GEV_STEP_MULTIPLY = 2,
+  GEV_STEP_TO_BAND = 3,
+  GEV_STEP_TO_TRIDIAG = 4,
+  GEV_STEP_SOLVE = 5,
+  GEV_STEP_BACK_TRIDIAG = 6,
+  GEV_STEP_BACK_BAND = 7,
+  GEV_STEP_MULT = 8,
+  GEV_STEP_REFINE = 9,
+  GEV_NSTEPS = 10
+};
+
+typedef struct {
+  int device;            /* CUDA device ordinal */
+  void* cuda_stream;     /* cudaStream_t on that device (NULL = legacy default stream) */
+  int prec;              /* gev_precision */
+  int band_b;            /* band width of the full->band step (0 = automatic; rounded up to 16, 32 or 64) */
+  int panel_nb;          /* block size of Cholesky / inversion (0 = automatic) */
+  double refine_tol;     /* mixed form: target residual (0 = 1e-11) */
+  int refine_max_iter;   /* mixed form: refinement iteration cap (0 = 4) */
+  size_t workspace_limit;/* bytes; 0 = no limit */
+  int timing;            /* non-zero: record per-step times into gev_report.ms */
+} gev_opts;
+
+typedef struct {
+  int info;                 /* NOT_SPD: pivot index + 1; otherwise 0 */
+  int deflated;             /* eigenpairs deflated in the top divide-and-conquer merge */
+  int refine_iters;         /* mixed form: refinement iterations performed */
+  int reused_factor;        /* 1 when the resident L^{-1} was used */
+  double refine_resid;      /* mixed form: last refinement residual ||A Y - Y L||_1/(||A||_1) */
+  double ms[GEV_NSTEPS];    /* per-step times when opts.timing != 0 */
+  size_t workspace_bytes;   /* device bytes held by the handle */
+} gev_report;
+
+/* Fill *opts with the defaults (device 0, default stream, GEV_PLAIN, automatic sizes). */
+void gev_default_opts(gev_opts* opts);
+
+/* Create a handle for problems of order n (1 <= n) and the given dtype; allocates the device
+   workspace on opts->device.  *out receives the handle (NULL on failure).  opts may be NULL
+   (defaults).  Returns GEV_ERR_OOM when the workspace does not fit (or exceeds workspace_limit). */
+int gev_setup(gev_sys** out, int n, int dtype, const gev_opts* opts);
+
+/* Solve H C = S C Lambda for the k lowest eigenpairs, 1 <= k <= n.
+   H, S   : device, lower triangles read (ldh, lds >= n).  S may be NULL after gev_reuse_factor(s,1)
+            and one successful solve: the resident L^{-1} of the last S is then reused.
+   evals  : device, k doubles, ascending.
+   C      : device, n x k, ldc >= n.
+   rep    : optional host struct.
+   Synchronises the handle's stream before returning. */
+int gev_solve(gev_sys* s, const void* H, int ldh, const void* S, int lds, int k, double* evals,
+              void* C, int ldc, gev_report* rep);
+
+/* enable != 0: keep L^{-1} resident after each solve so the next gev_solve may pass S = NULL
+   (SCF iterations with fixed overlap).  enable == 0 drops the resident factor. */
+int gev_reuse_factor(gev_sys* s, int enable);
+
+/* Release the handle and its workspace (s may be NULL). */
+int gev_free(gev_sys* s);
+
+/* Device bytes the handle would need for (n, dtype, opts); 0 on invalid arguments. */
+size_t gev_workspace_bytes(int n, int dtype, const gev_opts* opts);
+
+/* Error text for a return code (static string). */
+const char* gev_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GEV_H */

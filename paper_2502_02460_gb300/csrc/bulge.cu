@@ -1,0 +1,386 @@
+// Stage 2 of the two-stage tridiagonalisation: band (width b) -> real symmetric tridiagonal by
+// bulge chasing, B = Q2 T' Q2^H, and the back-transform Y = Q2 D Z (D: diagonal phases that make
+// the complex off-diagonal real).
+//
+// Sweep s (s = 0 .. n-3) annihilates column s below the subdiagonal with a Householder reflector
+// H(s,0) on rows W_0 = [s+1, s+1+b); applying it two-sided fills the b x b block below the window
+// (the bulge).  Task t >= 1 annihilates the first column of that block with H(s,t) on rows
+// W_t = [s+1+tb, s+1+(t+1)b), and so on down the band.  Footprint of task (s,t): rows
+// [p_t, p_{t+2}), columns [p_{t-1}, p_{t+1}) (p_t = s+1+tb).  Task (s+1,t) overlaps tasks
+// (s,t-1) .. (s,t+2) only, so sweep s+1 may run task t once sweep s has finished task t+2.
+//
+// GPU mapping: one persistent cooperative kernel; block q owns sweeps q, q+G, q+2G, ... and runs
+// their tasks in order, staging the three blocks of a task (L = (W_t, W_{t-1}), D = (W_t, W_t),
+// E = (W_{t+1}, W_t)) in shared memory; E stays resident as the next task's L.  A per-sweep
+// progress counter (release: __threadfence + store; acquire: volatile load + __threadfence, band
+// reads through L2 with __ldcg) orders the sweeps.  Every wait is bounded (kSpinLimit): on expiry
+// the kernel records ST_TIMEOUT, raises the abort flag and all blocks return.
+//
+// The band is stored compactly: element (i, j), 0 <= i-j < 2b, at band[(i-j) + j*ldb], ldb = 2b
+// (rows b+1 .. 2b-1 below the diagonal hold the bulge).
+#include <climits>
+
+#include "common.cuh"
+#include "coop.cuh"
+
+namespace gev {
+
+namespace {
+
+constexpr int NT = 256;
+
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+__device__ __forceinline__ zd warp_sum(zd v) { return make_zd(warp_sum(v.x), warp_sum(v.y)); }
+
+// Bounded acquire-wait until *flag >= target.  Thread 0 spins; returns false on timeout/abort.
+__device__ bool wait_ge(const int* flag, int target, int* status, int* abort_flag, int site) {
+  __shared__ int ok;
+  if (threadIdx.x == 0) {
+    int good = 1;
+    volatile const int* vf = flag;
+    volatile int* va = abort_flag;
+    long long it = 0;
+    while (*vf < target) {
+      if (*va) { good = 0; break; }
+      if (++it > kSpinLimit) {
+        atomicCAS(&status[ST_TIMEOUT], 0, site);
+        atomicExch(abort_flag, 1);
+        good = 0;
+        break;
+      }
+      __nanosleep(32);
+    }
+    __threadfence();
+    ok = good;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+template <class T>
+__global__ void __launch_bounds__(NT) k_bulge(int n, int b, T* band, int ldb, T* V2, T* tau2, int ntask,
+                                              int* progress, int* status, int* abort_flag) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int LD = b + 1;
+  T* Ls = reinterpret_cast<T*>(smraw);
+  T* Es = Ls + b * LD;
+  T* Ds = Es + b * LD;
+  T* v = Ds + b * LD;
+  T* y = v + b;
+  __shared__ T sh_tau, sh_beta, sh_scale;
+  __shared__ double sh_c;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  for (int s = blockIdx.x; s <= n - 3; s += gridDim.x) {
+    bool pendingL = false;
+    for (int t = 0;; ++t) {
+      const int p = s + 1 + t * b;
+      const int len = (p < n) ? min(b, n - p) : 0;
+      const int pp = p - b;
+      if (s > 0 && !wait_ge(&progress[s - 1], t + 3, status, abort_flag, 201)) return;
+      if (t > 0 && len <= 1) {
+        if (pendingL && len == 1)
+          for (int q = tid; q < b; q += NT) stcg_(&band[(b - q) + (long long)(pp + q) * ldb], Ls[q * LD]);
+        break;
+      }
+      // ---- generating vector x
+      for (int i = tid; i < len; i += NT)
+        v[i] = (t == 0) ? ldcg_(&band[(1 + i) + (long long)s * ldb]) : Ls[i];
+      __syncthreads();
+      if (warp == 0) {
+        double xn = 0.0;
+        for (int i = 1 + lane; i < len; i += 32) xn += abs2_(v[i]);
+        xn = warp_sum(xn);
+        if (lane == 0) {
+          const T alpha = v[0];
+          if (xn == 0.0 && im_(alpha) == 0.0) {
+            sh_tau = zero_<T>();
+            sh_beta = alpha;
+            sh_scale = zero_<T>();
+          } else {
+            const double nrm = sqrt(abs2_(alpha) + xn);
+            const T bt = from_re<T>(re_(alpha) >= 0.0 ? -nrm : nrm);
+            sh_tau = div_(bt - alpha, bt);
+            sh_beta = bt;
+            sh_scale = div_(from_re<T>(1.0), alpha - bt);
+          }
+        }
+      }
+      __syncthreads();
+      const T tau = sh_tau, beta = sh_beta, scale = sh_scale;
+      for (int i = tid; i < len; i += NT) v[i] = (i == 0) ? from_re<T>(1.0) : scale * v[i];
+      __syncthreads();
+      // ---- (i) the annihilated column, (ii) left update of the rest of L, store L
+      if (t == 0) {
+        for (int i = tid; i < len; i += NT)
+          stcg_(&band[(1 + i) + (long long)s * ldb], i == 0 ? beta : zero_<T>());
+      } else {
+        for (int i = tid; i < len; i += NT) Ls[i] = (i == 0) ? beta : zero_<T>();
+        const T ctau = conj_(tau);
+        for (int q = 1 + warp; q < b; q += NT / 32) {
+          T acc = zero_<T>();
+          for (int i = lane; i < len; i += 32) acc += cmul(v[i], Ls[i + q * LD]);
+          acc = ctau * warp_sum(acc);
+          for (int i = lane; i < len; i += 32) Ls[i + q * LD] -= v[i] * acc;
+        }
+        __syncthreads();
+        for (int idx = tid; idx < len * b; idx += NT) {
+          const int i = idx % len, q = idx / len;
+          stcg_(&band[(b + i - q) + (long long)(pp + q) * ldb], Ls[i + q * LD]);
+        }
+      }
+      // ---- (iii) two-sided update of the diagonal block
+      for (int idx = tid; idx < len * len; idx += NT) {
+        const int i = idx % len, j = idx / len;
+        if (i >= j) {
+          T val = ldcg_(&band[(i - j) + (long long)(p + j) * ldb]);
+          if (i == j) val = from_re<T>(re_(val));
+          Ds[i + j * LD] = val;
+          Ds[j + i * LD] = conj_(val);
+        }
+      }
+      __syncthreads();
+      for (int i = tid; i < len; i += NT) {
+        T acc = zero_<T>();
+        for (int j = 0; j < len; ++j) acc += Ds[i + j * LD] * v[j];
+        y[i] = acc;
+      }
+      __syncthreads();
+      if (warp == 0) {
+        T acc = zero_<T>();
+        for (int i = lane; i < len; i += 32) acc += cmul(v[i], y[i]);
+        acc = warp_sum(acc);
+        if (lane == 0) sh_c = 0.5 * abs2_(tau) * re_(acc);
+      }
+      __syncthreads();
+      for (int i = tid; i < len; i += NT) y[i] = tau * y[i] - sh_c * v[i];
+      __syncthreads();
+      for (int idx = tid; idx < len * len; idx += NT) {
+        const int i = idx % len, j = idx / len;
+        if (i >= j) {
+          T val = Ds[i + j * LD] - (mulc(y[i], v[j]) + mulc(v[i], y[j]));
+          if (i == j) val = from_re<T>(re_(val));
+          stcg_(&band[(i - j) + (long long)(p + j) * ldb], val);
+        }
+      }
+      __syncthreads();
+      // ---- (iv) right update of the block below: creates the next bulge
+      const int p2 = p + len;
+      if (p2 < n) {
+        const int len2 = min(b, n - p2);
+        for (int idx = tid; idx < len2 * len; idx += NT) {
+          const int r = idx % len2, q = idx / len2;
+          Es[r + q * LD] = ldcg_(&band[(len + r - q) + (long long)(p + q) * ldb]);
+        }
+        __syncthreads();
+        for (int r = tid; r < len2; r += NT) {
+          T acc = zero_<T>();
+          for (int q = 0; q < len; ++q) acc += Es[r + q * LD] * v[q];
+          y[r] = tau * acc;
+        }
+        __syncthreads();
+        for (int idx = tid; idx < len2 * len; idx += NT) {
+          const int r = idx % len2, q = idx / len2;
+          Es[r + q * LD] -= mulc(y[r], v[q]);
+        }
+        pendingL = true;
+      } else {
+        pendingL = false;
+      }
+      // ---- keep the reflector for the back-transform
+      const long long rid = (long long)s * ntask + t;
+      for (int i = tid; i < b; i += NT) V2[rid * b + i] = (i < len) ? v[i] : zero_<T>();
+      if (tid == 0) tau2[rid] = tau;
+      __syncthreads();
+      if (tid == 0) {
+        __threadfence();
+        atomicExch(&progress[s], t + 1);
+      }
+      T* tmp = Ls;
+      Ls = Es;
+      Es = tmp;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      atomicExch(&progress[s], INT_MAX);
+    }
+  }
+}
+
+// d = Re diag, e = |subdiag| with the phase recursion phi_0 = 1, phi_{i+1} = phi_i eps_i/|eps_i|
+// (complex), or e = subdiag (real).  One block: the phase recursion is sequential.
+template <class T>
+__global__ void k_tridiag_out(int n, const T* band, int ldb, double* d, double* e, T* phase) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) d[i] = re_(band[(long long)i * ldb]);
+  if constexpr (is_cx<T>::value) {
+    if (threadIdx.x == 0) {
+      T ph = from_re<T>(1.0);
+      phase[0] = ph;
+      for (int i = 0; i + 1 < n; ++i) {
+        const T eps = band[1 + (long long)i * ldb];
+        const double a = abs_(eps);
+        e[i] = a;
+        if (a > 0.0) ph = ph * make_zd(eps.x / a, eps.y / a);
+        phase[i + 1] = ph;
+      }
+    }
+  } else {
+    for (int i = threadIdx.x; i + 1 < n; i += blockDim.x) e[i] = band[1 + (long long)i * ldb];
+  }
+}
+
+// Y = D Z (real Z -> scalar type; D = diag(phase) for complex data, identity for real).
+template <class T>
+__global__ void k_phase_rows(int n, int k, const double* Z, long long ldz, const T* phase, T* Y,
+                             long long ldy) {
+  const long long total = (long long)n * k;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % n), c = (int)(t / n);
+    const double z = Z[i + c * ldz];
+    if constexpr (is_cx<T>::value) Y[i + c * ldy] = z * phase[i];
+    else Y[i + c * ldy] = z;
+  }
+}
+
+// Y <- Q2 Y.  Block = one thread per column of a BNc-wide column block.  Reflectors are applied in
+// groups of G consecutive sweeps (last group first); inside a group, for t = 0, 1, ... the rows
+// touched by H(s0..s0+G-1, t) form a window of b+G-1 rows, staged in shared memory, to which the
+// group's reflectors are applied in the order s = s0+G-1 .. s0.  (Within a sweep the reflectors act
+// on disjoint rows and commute; H(s',t') with s' > s must stay to the right of H(s,t) only for
+// t' in {t-1, t}; the order "t ascending, s descending" respects that.)
+template <class T>
+__global__ void k_bt_bulge(int n, int k, int b, int G, const T* V2, const T* tau2, int ntask, T* Y,
+                           long long ldy) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int BNc = blockDim.x;
+  const int c0 = blockIdx.x * BNc;
+  const int c = threadIdx.x;
+  const int LDZ = BNc + 1;
+  const int WR = b + G - 1;
+  T* Zw = reinterpret_cast<T*>(smraw);          // WR x BNc (row-major, padded)
+  T* Vs = Zw + (size_t)WR * LDZ;                 // G x b
+  T* ts = Vs + (size_t)G * b;                    // G
+  const int ncols = min(BNc, k - c0);
+  const int last_sweep = n - 3;
+  if (last_sweep < 0) return;
+  const int ngroups = last_sweep / G + 1;
+  for (int g = ngroups - 1; g >= 0; --g) {
+    const int s0 = g * G;
+    const int s1 = min(s0 + G - 1, last_sweep);
+    for (int t = 0; t < ntask; ++t) {
+      const int w0 = s0 + 1 + t * b;
+      if (w0 >= n) break;
+      const int w1 = min(n, s1 + 1 + t * b + b);
+      const int rows = w1 - w0;
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < rows * ncols; idx += BNc) {
+        const int r = idx % rows, cc = idx / rows;
+        Zw[r * LDZ + cc] = Y[(w0 + r) + (long long)(c0 + cc) * ldy];
+      }
+      for (int idx = threadIdx.x; idx < (s1 - s0 + 1) * b; idx += BNc) {
+        const int q = idx / b, i = idx % b;
+        Vs[q * b + i] = V2[((long long)(s0 + q) * ntask + t) * b + i];
+      }
+      for (int q = threadIdx.x; q <= s1 - s0; q += BNc) ts[q] = tau2[(long long)(s0 + q) * ntask + t];
+      __syncthreads();
+      if (c < ncols) {
+        for (int q = s1 - s0; q >= 0; --q) {
+          const T tau = ts[q];
+          if (tau == zero_<T>()) continue;
+          const int p = s0 + q + 1 + t * b;
+          const int len = min(b, n - p);
+          const int off = p - w0;
+          const T* vq = Vs + q * b;
+          T acc = zero_<T>();
+          for (int i = 0; i < len; ++i) acc += cmul(vq[i], Zw[(off + i) * LDZ + c]);
+          acc = tau * acc;
+          for (int i = 0; i < len; ++i) Zw[(off + i) * LDZ + c] -= vq[i] * acc;
+        }
+      }
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < rows * ncols; idx += BNc) {
+        const int r = idx % rows, cc = idx / rows;
+        Y[(w0 + r) + (long long)(c0 + cc) * ldy] = Zw[r * LDZ + cc];
+      }
+    }
+  }
+}
+
+template <class T> size_t bulge_smem(int b) { return sizeof(T) * ((size_t)3 * b * (b + 1) + 2 * b) + 64; }
+
+}  // namespace
+
+template <class T> int hb2st(Sys& s, double* d, double* e) {
+  const int n = s.n, b = s.band_b_used;
+  const int ldb = 2 * b;
+  T* band = (T*)s.band;
+  if (n <= 2) {
+    // already tridiagonal
+  } else {
+    if (b > 64) return GEV_ERR_UNSUPPORTED;
+    const size_t smem = bulge_smem<T>(b);
+    static bool attr = false;
+    if (!attr) {
+      GEV_CUDA_TRY(cudaFuncSetAttribute(k_bulge<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+      attr = true;
+    }
+    int per_sm = 0;
+    GEV_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bulge<T>, NT, smem));
+    if (per_sm < 1) return GEV_ERR_UNSUPPORTED;
+    int G = per_sm * s.sms;
+    if (G > n - 2) G = n - 2;
+    GEV_CUDA_TRY(cudaMemsetAsync(s.prog, 0, sizeof(int) * (size_t)n, s.stream));
+    GEV_CUDA_TRY(cudaMemsetAsync(s.tau2, 0, s.es() * (size_t)n * s.ntask, s.stream));
+    GEV_CUDA_TRY(cudaMemsetAsync(&s.status[ST_ABORT], 0, sizeof(int), s.stream));
+    int nn = n, bb = b, lb = ldb, nt = s.ntask;
+    T* V2 = (T*)s.V2;
+    T* tau2 = (T*)s.tau2;
+    int* prog = s.prog;
+    int* st = s.status;
+    int* ab = &s.status[ST_ABORT];
+    void* args[] = {&nn, &bb, &band, &lb, &V2, &tau2, &nt, &prog, &st, &ab};
+    GEV_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_bulge<T>, dim3(G), dim3(NT), args, smem, s.stream));
+  }
+  k_tridiag_out<T><<<1, 256, 0, s.stream>>>(n, band, ldb, d, e, (T*)s.phase);
+  GEV_TRY(last_error());
+  s.have_tridiag_refl = true;
+  return 0;
+}
+
+// Y (n x k) = Q2 D Z for real Z.
+template <class T> int bt_hb2st(Sys& s, const double* Z, int ldz, int k, T* Y, int ldy) {
+  const int n = s.n, b = s.band_b_used;
+  {
+    long long total = (long long)n * k;
+    unsigned blocks = cdiv(total, 256);
+    if (blocks > 16u * s.sms) blocks = 16u * s.sms;
+    k_phase_rows<T><<<blocks, 256, 0, s.stream>>>(n, k, Z, ldz, (const T*)s.phase, Y, ldy);
+    GEV_TRY(last_error());
+  }
+  if (n <= 2) return 0;
+  int BNc = 32;
+  while (BNc < 128 && cdiv(k, BNc * 2) >= (unsigned)s.sms) BNc *= 2;
+  const int G = b;
+  const size_t smem = sizeof(T) * ((size_t)(b + G - 1) * (BNc + 1) + (size_t)G * b + G) + 64;
+  static bool attr = false;
+  if (!attr) {
+    GEV_CUDA_TRY(cudaFuncSetAttribute(k_bt_bulge<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    attr = true;
+  }
+  k_bt_bulge<T><<<cdiv(k, BNc), BNc, smem, s.stream>>>(n, k, b, G, (const T*)s.V2, (const T*)s.tau2,
+                                                        s.ntask, Y, ldy);
+  return last_error();
+}
+
+template int hb2st<double>(Sys&, double*, double*);
+template int hb2st<zd>(Sys&, double*, double*);
+template int bt_hb2st<double>(Sys&, const double*, int, int, double*, int);
+template int bt_hb2st<zd>(Sys&, const double*, int, int, zd*, int);
+
+}  // namespace gev

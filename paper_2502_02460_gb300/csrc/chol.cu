@@ -1,0 +1,212 @@
+// Reduction steps 1-3 of the section "Current Status of the Implementation" and the final
+// back-multiplication (Table 1: Choles., Invert, Multiply, Mult.):
+//   potrf : S = L L^H, blocked right-looking; diagonal blocks factored (and inverted) in one CTA,
+//           panel solve L21 = A21 L11^{-H} as a GEMM with the inverted diagonal block, trailing
+//           update A22 -= L21 L21^H as a lower-only GEMM.
+//   trtri : X = L^{-1}, blocked from the last block column: X21 = -X22 L21 X11.
+//   hegst : A = X H X^H with H = B + B^H, B = tril(H) with halved diagonal:
+//           P = X B (lower x lower -> lower), M = P X^H, A = M + M^H   (N^3 flops in total).
+//   mult  : C = X^H Y (upper-triangular operand, N^2 k flops).
+#include "common.cuh"
+
+namespace gev {
+
+namespace {
+
+constexpr int NBMAX = 64;
+constexpr int LDS = NBMAX + 1;
+
+// X <- L^{-1} for the jb x jb lower-triangular L in shared memory (both column-major, ld LDS).
+template <class T>
+__device__ void inv_lower_smem(int jb, const T* L, T* X) {
+  for (int c = threadIdx.x; c < jb; c += blockDim.x) {
+    for (int i = 0; i < jb; ++i) {
+      T v = zero_<T>();
+      if (i >= c) {
+        T acc = (i == c) ? from_re<T>(1.0) : zero_<T>();
+        for (int p = c; p < i; ++p) acc -= L[i + p * LDS] * X[p + c * LDS];
+        v = (1.0 / re_(L[i + i * LDS])) * acc;
+      }
+      X[i + c * LDS] = v;
+    }
+  }
+}
+
+// Factor the jb x jb diagonal block in place (lower) and write its inverse to Dinv.
+template <class T>
+__global__ void k_potrf_diag(int jb, T* A, long long lda, T* Dinv, long long ldd, int* status, int j0) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* L = reinterpret_cast<T*>(smraw);
+  T* X = L + NBMAX * LDS;
+  __shared__ int fail;
+  const int tid = threadIdx.x;
+  if (tid == 0) fail = 0;
+  for (int t = tid; t < jb * jb; t += blockDim.x) {
+    int i = t % jb, j = t / jb;
+    L[i + j * LDS] = (i >= j) ? A[i + j * lda] : zero_<T>();
+  }
+  __syncthreads();
+  for (int p = 0; p < jb; ++p) {
+    if (tid == 0) {
+      double d = re_(L[p + p * LDS]);
+      if (!(d > 0.0)) {
+        fail = 1;
+        atomicCAS(&status[ST_NOT_SPD], 0, j0 + p + 1);
+      } else {
+        L[p + p * LDS] = from_re<T>(sqrt(d));
+      }
+    }
+    __syncthreads();
+    if (fail) return;
+    const double inv = 1.0 / re_(L[p + p * LDS]);
+    for (int i = p + 1 + tid; i < jb; i += blockDim.x) L[i + p * LDS] = inv * L[i + p * LDS];
+    __syncthreads();
+    const int r = jb - p - 1;
+    for (int t = tid; t < r * r; t += blockDim.x) {
+      int i = p + 1 + t % r, j = p + 1 + t / r;
+      if (j <= i) L[i + j * LDS] -= mulc(L[i + p * LDS], L[j + p * LDS]);
+    }
+    __syncthreads();
+  }
+  inv_lower_smem(jb, L, X);
+  __syncthreads();
+  for (int t = tid; t < jb * jb; t += blockDim.x) {
+    int i = t % jb, j = t / jb;
+    A[i + j * lda] = (i >= j) ? L[i + j * LDS] : zero_<T>();
+    Dinv[i + j * ldd] = X[i + j * LDS];
+  }
+}
+
+// Invert every diagonal block of the lower-triangular L: block q -> Dinv[:, q*nb ...] (ld nb).
+template <class T>
+__global__ void k_inv_diag_blocks(int n, int nb, const T* A, long long lda, T* Dinv) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* L = reinterpret_cast<T*>(smraw);
+  T* X = L + NBMAX * LDS;
+  const int j0 = blockIdx.x * nb;
+  const int jb = min(nb, n - j0);
+  for (int t = threadIdx.x; t < jb * jb; t += blockDim.x) {
+    int i = t % jb, j = t / jb;
+    L[i + j * LDS] = (i >= j) ? A[(j0 + i) + (long long)(j0 + j) * lda] : zero_<T>();
+  }
+  __syncthreads();
+  inv_lower_smem(jb, L, X);
+  __syncthreads();
+  for (int t = threadIdx.x; t < jb * jb; t += blockDim.x) {
+    int i = t % jb, j = t / jb;
+    Dinv[i + (long long)(j0 + j) * nb] = X[i + j * LDS];
+  }
+}
+
+template <class T> size_t diag_smem() { return sizeof(T) * 2 * NBMAX * LDS; }
+
+template <class T> int set_smem_attrs() {
+  static bool done = false;
+  if (!done) {
+    GEV_CUDA_TRY(cudaFuncSetAttribute(k_potrf_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)diag_smem<T>()));
+    GEV_CUDA_TRY(cudaFuncSetAttribute(k_inv_diag_blocks<T>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)diag_smem<T>()));
+    done = true;
+  }
+  return 0;
+}
+
+}  // namespace
+
+template <class T> int potrf(Sys& s, T* A, int lda) {
+  const int n = s.n, nb = s.nb;
+  GEV_TRY(set_smem_attrs<T>());
+  T* Dinv = (T*)s.dinv;  // nb x nb (first block slot)
+  T* P = (T*)s.Pn;       // n x nb panel
+  const T one = from_re<T>(1.0), mone = from_re<T>(-1.0), zero = zero_<T>();
+  for (int j = 0; j < n; j += nb) {
+    const int jb = nb < n - j ? nb : n - j;
+    T* Ajj = A + j + (long long)j * lda;
+    k_potrf_diag<T><<<1, 256, diag_smem<T>(), s.stream>>>(jb, Ajj, lda, Dinv, nb, s.status, j);
+    GEV_TRY(last_error());
+    const int m = n - j - jb;
+    if (m <= 0) break;
+    T* A21 = A + (j + jb) + (long long)j * lda;
+    T* A22 = A + (j + jb) + (long long)(j + jb) * lda;
+    // L21 = A21 L11^{-H}
+    GemmP<T> g = gp<T>(m, jb, jb, 0, 2, one, A21, lda, Dinv, nb, zero, P, n);
+    g.tri_b = 2;
+    gemm(s, g);
+    // A22 -= L21 L21^H (lower)
+    g = gp<T>(m, m, jb, 0, 2, mone, P, n, P, n, one, A22, lda);
+    g.c_lower = 1;
+    gemm(s, g);
+    GEV_TRY(copy2d<T>(s, m, jb, P, n, A21, lda));
+  }
+  GEV_TRY(zero_upper<T>(s, n, A, lda));
+  return last_error();
+}
+
+template <class T> int trtri(Sys& s, T* A, int lda) {
+  const int n = s.n, nb = s.nb;
+  GEV_TRY(set_smem_attrs<T>());
+  T* Dinv = (T*)s.dinv;  // nb x n: all diagonal-block inverses
+  T* T1 = (T*)s.Pn;
+  const T one = from_re<T>(1.0), mone = from_re<T>(-1.0), zero = zero_<T>();
+  const int nblk = (n + nb - 1) / nb;
+  k_inv_diag_blocks<T><<<nblk, 256, diag_smem<T>(), s.stream>>>(n, nb, A, lda, Dinv);
+  GEV_TRY(last_error());
+  for (int q = nblk - 1; q >= 0; --q) {
+    const int j = q * nb;
+    const int jb = nb < n - j ? nb : n - j;
+    const int m = n - j - jb;
+    if (m > 0) {
+      T* L21 = A + (j + jb) + (long long)j * lda;
+      T* X22 = A + (j + jb) + (long long)(j + jb) * lda;
+      GemmP<T> g = gp<T>(m, jb, m, 0, 0, one, X22, lda, L21, lda, zero, T1, n);
+      g.tri_a = 1;
+      gemm(s, g);
+      g = gp<T>(m, jb, jb, 0, 0, mone, T1, n, Dinv + (long long)j * nb, nb, zero, L21, lda);
+      g.tri_b = 1;
+      gemm(s, g);
+    }
+    GEV_TRY(copy2d<T>(s, jb, jb, Dinv + (long long)j * nb, nb, A + j + (long long)j * lda, lda));
+  }
+  GEV_TRY(zero_upper<T>(s, n, A, lda));
+  return last_error();
+}
+
+template <class T> int hegst(Sys& s, const T* H, int ldh, const T* X, int ldx, T* A, int lda) {
+  const int n = s.n;
+  T* B = (T*)s.W1;
+  const T one = from_re<T>(1.0), zero = zero_<T>();
+  GEV_TRY(tril_halfdiag<T>(s, n, H, ldh, B, n));
+  // P = X B (both lower -> lower), into A
+  GemmP<T> g = gp<T>(n, n, n, 0, 0, one, X, ldx, B, n, zero, A, lda);
+  g.tri_a = 1;
+  g.tri_b = 1;
+  g.c_lower = 1;
+  gemm(s, g);
+  // M = P X^H, into B (full)
+  g = gp<T>(n, n, n, 0, 2, one, A, lda, X, ldx, zero, B, n);
+  g.tri_a = 1;
+  g.tri_b = 2;
+  gemm(s, g);
+  GEV_TRY(herm_sum<T>(s, n, B, n, A, lda));
+  return last_error();
+}
+
+template <class T> int mult(Sys& s, const T* X, int ldx, const T* Y, int ldy, int k, T* C, int ldc) {
+  const int n = s.n;
+  GemmP<T> g = gp<T>(n, k, n, 2, 0, from_re<T>(1.0), X, ldx, Y, ldy, zero_<T>(), C, ldc);
+  g.tri_a = 2;
+  gemm(s, g);
+  return last_error();
+}
+
+#define GEV_INST(T)                                                     \
+  template int potrf<T>(Sys&, T*, int);                                 \
+  template int trtri<T>(Sys&, T*, int);                                 \
+  template int hegst<T>(Sys&, const T*, int, const T*, int, T*, int);   \
+  template int mult<T>(Sys&, const T*, int, const T*, int, int, T*, int);
+GEV_INST(double)
+GEV_INST(zd)
+#undef GEV_INST
+
+}  // namespace gev

@@ -1,0 +1,227 @@
+// Shared definitions of the GB300 generalized eigensolver: scalar types, the handle, launchers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <cstdio>
+
+#include "gev.h"
+#include "gev_steps.h"
+
+namespace gev {
+
+// ------------------------------------------------------------------------------ scalar types --
+// complex128, interleaved (re, im) like C99 double complex.
+struct alignas(16) zd {
+  double x, y;
+};
+
+__host__ __device__ __forceinline__ zd make_zd(double a, double b) { return zd{a, b}; }
+__host__ __device__ __forceinline__ zd operator+(zd a, zd b) { return {a.x + b.x, a.y + b.y}; }
+__host__ __device__ __forceinline__ zd operator-(zd a, zd b) { return {a.x - b.x, a.y - b.y}; }
+__host__ __device__ __forceinline__ zd operator-(zd a) { return {-a.x, -a.y}; }
+__host__ __device__ __forceinline__ zd operator*(zd a, zd b) {
+  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+__host__ __device__ __forceinline__ zd operator*(double s, zd a) { return {s * a.x, s * a.y}; }
+__host__ __device__ __forceinline__ zd operator*(zd a, double s) { return {s * a.x, s * a.y}; }
+__host__ __device__ __forceinline__ zd& operator+=(zd& a, zd b) { a.x += b.x; a.y += b.y; return a; }
+__host__ __device__ __forceinline__ zd& operator-=(zd& a, zd b) { a.x -= b.x; a.y -= b.y; return a; }
+__host__ __device__ __forceinline__ bool operator==(zd a, zd b) { return a.x == b.x && a.y == b.y; }
+__host__ __device__ __forceinline__ bool operator!=(zd a, zd b) { return !(a == b); }
+
+__host__ __device__ __forceinline__ double conj_(double a) { return a; }
+__host__ __device__ __forceinline__ zd conj_(zd a) { return {a.x, -a.y}; }
+__host__ __device__ __forceinline__ double re_(double a) { return a; }
+__host__ __device__ __forceinline__ double re_(zd a) { return a.x; }
+__host__ __device__ __forceinline__ double im_(double) { return 0.0; }
+__host__ __device__ __forceinline__ double im_(zd a) { return a.y; }
+__host__ __device__ __forceinline__ double abs2_(double a) { return a * a; }
+__host__ __device__ __forceinline__ double abs2_(zd a) { return a.x * a.x + a.y * a.y; }
+__host__ __device__ __forceinline__ double abs_(double a) { return fabs(a); }
+__host__ __device__ __forceinline__ double abs_(zd a) { return hypot(a.x, a.y); }
+template <class T> __host__ __device__ __forceinline__ T from_re(double a);
+template <> __host__ __device__ __forceinline__ double from_re<double>(double a) { return a; }
+template <> __host__ __device__ __forceinline__ zd from_re<zd>(double a) { return {a, 0.0}; }
+template <class T> __host__ __device__ __forceinline__ T zero_() { return from_re<T>(0.0); }
+// a * conj(b) and conj(a) * b
+__host__ __device__ __forceinline__ double mulc(double a, double b) { return a * b; }
+__host__ __device__ __forceinline__ zd mulc(zd a, zd b) { return a * conj_(b); }
+__host__ __device__ __forceinline__ double cmul(double a, double b) { return a * b; }
+__host__ __device__ __forceinline__ zd cmul(zd a, zd b) { return conj_(a) * b; }
+__host__ __device__ __forceinline__ zd div_(zd a, zd b) {
+  double d = b.x * b.x + b.y * b.y;
+  return {(a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d};
+}
+__host__ __device__ __forceinline__ double div_(double a, double b) { return a / b; }
+
+// L2-coherent loads/stores (bypass L1) for data another block may have written during the kernel.
+__device__ __forceinline__ double ldcg_(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ zd ldcg_(const zd* p) {
+  double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+  return make_zd(v.x, v.y);
+}
+__device__ __forceinline__ void stcg_(double* p, double v) { __stcg(p, v); }
+__device__ __forceinline__ void stcg_(zd* p, zd v) {
+  __stcg(reinterpret_cast<double2*>(p), make_double2(v.x, v.y));
+}
+
+template <class T> struct is_cx { static constexpr bool value = false; };
+template <> struct is_cx<zd> { static constexpr bool value = true; };
+
+// ------------------------------------------------------------------------- status word slots --
+enum StatusSlot {
+  ST_NOT_SPD = 0,       // pivot index + 1 of the first non-positive Cholesky pivot
+  ST_TIMEOUT = 1,       // non-zero: a bounded device wait gave up (value = site code)
+  ST_NOCONV = 2,        // non-zero: an iteration cap was hit (value = site code)
+  ST_DEFLATED = 3,      // eigenpairs deflated in the top merge
+  ST_BARRIER_GEN = 4,   // grid-barrier generation counter (cooperative kernels)
+  ST_BARRIER_CNT = 5,   // grid-barrier arrival counter
+  ST_ABORT = 6,         // non-zero once a cooperative kernel gave up waiting
+  ST_COUNT = 16
+};
+
+// Bounded spin limit for every device-side wait (iterations of a ~100 ns nanosleep loop).
+constexpr long long kSpinLimit = 20000000;  // ~2 s
+
+// -------------------------------------------------------------------------------------- GEMM --
+// C[M x N] = alpha op(A) op(B) + beta C, column-major.
+//   ta/tb: 0 = N, 1 = T, 2 = C (conjugate transpose)
+//   tri_a: 1 -> op(A)[i,k] = 0 for k > i (lower); 2 -> zero for k < i (upper)
+//   tri_b: 1 -> op(B)[k,j] = 0 for k < j (lower); 2 -> zero for k > j (upper)
+//   c_lower: only entries i >= j of C are computed and written.
+// Zero patterns are applied element by element when loading, so the stored "zero" triangle of a
+// triangular operand is never read.
+template <class T> struct GemmP {
+  int M, N, K;
+  int ta, tb;
+  int tri_a, tri_b, c_lower;
+  T alpha, beta;
+  const T* A;
+  long long lda;
+  const T* B;
+  long long ldb;
+  T* C;
+  long long ldc;
+  int ksplit;  // set by the launcher
+  T* ws;       // split-K partials (launcher-owned)
+};
+
+struct Sys;
+
+template <class T> void gemm(Sys& s, GemmP<T> p);
+template <class T> GemmP<T> gp(int M, int N, int K, int ta, int tb, T alpha, const T* A, long long lda,
+                               const T* B, long long ldb, T beta, T* C, long long ldc) {
+  GemmP<T> p{};
+  p.M = M; p.N = N; p.K = K; p.ta = ta; p.tb = tb; p.alpha = alpha; p.beta = beta;
+  p.A = A; p.lda = lda; p.B = B; p.ldb = ldb; p.C = C; p.ldc = ldc;
+  return p;
+}
+
+// ---------------------------------------------------------------------------------- the handle --
+struct Sys {
+  int n = 0;
+  int dtype = GEV_F64;
+  gev_opts opts{};
+  cudaStream_t stream = nullptr;
+  int nb = 64;      // Cholesky / inversion block
+  int b = 64;       // band width of the full -> band step
+  int sms = 152;
+
+  // workspace (device)
+  char* base = nullptr;
+  size_t bytes = 0;
+  void* A = nullptr;      // n x n working matrix (element size es)
+  void* X = nullptr;      // n x n resident L^{-1}
+  void* W1 = nullptr;     // n x n scratch
+  void* V1 = nullptr;     // n x n compact-WY vectors of the full -> band step
+  void* T1 = nullptr;     // b x n triangular factors of the full -> band step
+  void* dinv = nullptr;   // nb x n inverted diagonal blocks (Cholesky / inversion)
+  void* Pn = nullptr;     // n x 2b panel scratch (x 4 buffers)
+  void* small = nullptr;  // b x b scratch (x 4)
+  void* splitws = nullptr;  // split-K partials
+  size_t splitws_bytes = 0;
+  void* band = nullptr;   // compact band, ldband x n
+  int ldband = 0;
+  void* V2 = nullptr;     // bulge-chasing reflectors, b x (n * ntask)
+  void* tau2 = nullptr;   // (n * ntask)
+  int ntask = 0;          // max tasks per sweep
+  void* phase = nullptr;  // complex: diagonal phases folded into back-transform 2 (n)
+  double* d = nullptr;    // tridiagonal diagonal (n)
+  double* e = nullptr;    // off-diagonal (n)
+  double* w = nullptr;    // eigenvalues (n)
+  double* Q = nullptr;    // n x n divide-and-conquer eigenvectors
+  double* Q2 = nullptr;   // n x n divide-and-conquer scratch
+  void* dcws = nullptr;   // divide-and-conquer per-level workspace
+  size_t dcws_bytes = 0;
+  void* Yk = nullptr;     // n x n back-transformed vectors (element size es)
+  double* Zk = nullptr;   // n x n eigenvectors of the tridiagonal (divide-and-conquer output)
+  int* prog = nullptr;    // n per-sweep progress counters of the bulge chasing
+  int nsbr_panels = 0;    // panels of the last full -> band reduction
+  void* panelws = nullptr;  // cooperative panel partial sums
+  size_t panelws_bytes = 0;
+  int* status = nullptr;  // device status words (ST_COUNT ints)
+  cudaEvent_t ev[GEV_NSTEPS + 1] = {};
+  int* status_h = nullptr;  // pinned host mirror
+
+  bool have_factor = false;
+  bool reuse = false;
+  bool have_band = false;
+  bool have_tridiag_refl = false;
+  int band_b_used = 0;
+
+  size_t es() const { return dtype == GEV_C128 ? 16 : 8; }
+};
+
+// CUDA error handling: every launcher returns a gev error code.
+#define GEV_CUDA_TRY(expr)                                                          \
+  do {                                                                              \
+    cudaError_t _e = (expr);                                                        \
+    if (_e != cudaSuccess) {                                                        \
+      fprintf(stderr, "gev: CUDA error %s at %s:%d\n", cudaGetErrorString(_e), __FILE__, \
+              __LINE__);                                                            \
+      return GEV_ERR_CUDA;                                                          \
+    }                                                                               \
+  } while (0)
+
+#define GEV_TRY(expr)        \
+  do {                       \
+    int _r = (expr);         \
+    if (_r != 0) return _r;  \
+  } while (0)
+
+inline int last_error() {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    fprintf(stderr, "gev: CUDA launch error %s\n", cudaGetErrorString(e));
+    return GEV_ERR_CUDA;
+  }
+  return 0;
+}
+
+inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
+
+// ---------------------------------------------------------------------------- step launchers --
+template <class T> int potrf(Sys& s, T* A, int lda);
+template <class T> int trtri(Sys& s, T* A, int lda);
+template <class T> int hegst(Sys& s, const T* H, int ldh, const T* X, int ldx, T* A, int lda);
+template <class T> int mult(Sys& s, const T* X, int ldx, const T* Y, int ldy, int k, T* C, int ldc);
+template <class T> int he2hb(Sys& s, T* A, int lda, int b);
+template <class T> int hb2st(Sys& s, double* d, double* e);
+int stedc(Sys& s, const double* d, const double* e, int k, double* w, double* Z, int ldz, int* deflated);
+template <class T> int back(Sys& s, const double* Z, int ldz, int k, T* Y, int ldy);
+template <class T> int bt_he2hb(Sys& s, T* Y, int ldy, int k);
+template <class T> int bt_hb2st(Sys& s, const double* Z, int ldz, int k, T* Y, int ldy);
+
+// element-wise helpers (kernels in util.cu)
+template <class T> int copy_lower(Sys& s, int n, const T* S, int lds, T* A, int lda);   // A = tril(S), upper 0
+template <class T> int tril_halfdiag(Sys& s, int n, const T* H, int ldh, T* B, int ldb); // B = tril(H), diag/2
+template <class T> int herm_sum(Sys& s, int n, const T* M, int ldm, T* A, int lda);     // A = M + M^H (full)
+template <class T> int mirror_lower(Sys& s, int n, T* A, int lda);                        // upper <- conj(lower)
+template <class T> int zero_upper(Sys& s, int n, T* A, int lda);                          // strict upper <- 0
+template <class T> int copy2d(Sys& s, int m, int n, const T* src, long long lds, T* dst, long long ldd);
+template <class T> int normalize_phase(Sys& s, int n, int k, T* C, int ldc);
+int sync_status(Sys& s);  // synchronise the stream, copy the status words to the host mirror
+
+}  // namespace gev

@@ -1,0 +1,306 @@
+// Stage 1 of the two-stage tridiagonalisation ("ELPA2", section "Usability and Tutorials"):
+// full Hermitian A -> band B of width b, A = Q1 B Q1^H, and the matching back-transform Y = Q1 Z.
+//
+// For each panel (columns j0..j0+b-1, rows r0 = j0+b .. n-1):
+//   1. Householder QR of the m x b panel (m = n - r0) in ONE cooperative kernel: the panel rows are
+//      spread over all SMs and stay in shared memory; each column needs two bounded grid barriers
+//      (norm, then the reflector's inner products, which also give the column of the compact-WY
+//      factor T).  Q = H_0 ... H_{b-1} = I - Y T Y^H, T upper triangular.
+//   2. Two-sided update of the trailing block A22 <- Q^H A22 Q by GEMMs:
+//        W = A22 Y T,  U = T^H (Y^H W),  V = W - Y U / 2,  A22 -= Y V^H + V Y^H (lower), mirror.
+// Y is kept explicitly (unit diagonal, zeros above) in the handle's V1 at the panel's position and
+// T in T1, for the back-transform  Y_out = Q1 Z = Q_0 (Q_1 (... Q_last Z)).
+#include "common.cuh"
+#include "coop.cuh"
+
+namespace gev {
+
+namespace {
+
+constexpr int NT = 256;
+
+template <class T>
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+  return t;  // valid in thread 0
+}
+
+template <class T>
+__global__ void __launch_bounds__(NT) k_panel_qr(int m, int b, T* P, long long ldp, T* Y, long long ldy,
+                                                 T* Tm, double* nrm_part, T* w_part, T* alpha_g,
+                                                 GridBar gb, int R, int use_smem) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int blk = blockIdx.x, tid = threadIdx.x;
+  const int lo = blk * R;
+  const int hi = min(m, lo + R);
+  const int rows = max(0, hi - lo);
+  const long long lds = R | 1;
+  T* sm = reinterpret_cast<T*>(smraw);
+  T* scratch = use_smem ? sm + lds * b : sm;
+  T* red2 = scratch;          // NT entries
+  T* wv = scratch + NT;       // b entries
+  double* red = reinterpret_cast<double*>(wv + b);  // 32 doubles
+  __shared__ T sh_tau, sh_beta, sh_scale;
+  __shared__ int sh_trivial;
+
+  T* base = use_smem ? sm : P + lo;
+  const long long ld = use_smem ? lds : ldp;
+  if (use_smem) {
+    for (int idx = tid; idx < rows * b; idx += NT) {
+      int r = idx % rows, c = idx / rows;
+      sm[r + c * lds] = P[(lo + r) + c * ldp];
+    }
+    __syncthreads();
+  }
+  const int NG = NT / b;  // row groups (b is a power of two <= 128)
+  const int jj = tid % b, grp = tid / b;
+
+  for (int c = 0; c < b; ++c) {
+    if (c >= m) {
+      if (blk == 0 && tid < b) Tm[tid + c * b] = zero_<T>();
+      continue;
+    }
+    // ---- A: squared norm of the column below the pivot row
+    double ss = 0.0;
+    for (int r = max(0, c + 1 - lo) + tid; r < rows; r += NT) ss += abs2_(base[r + c * ld]);
+    double tot = block_sum<T>(ss, red);
+    if (tid == 0) {
+      nrm_part[blk] = tot;
+      if (lo <= c && c < hi) alpha_g[0] = base[(c - lo) + c * ld];
+    }
+    if (!grid_sync(gb, 101)) return;
+    // ---- B: reflector
+    if (tid == 0) {
+      double xn = 0.0;
+      for (int q = 0; q < (int)gridDim.x; ++q) xn += ldcg_(&nrm_part[q]);
+      T alpha = ldcg_(alpha_g);
+      int trivial = (xn == 0.0 && im_(alpha) == 0.0);
+      if (trivial) {
+        sh_tau = zero_<T>();
+        sh_beta = alpha;
+        sh_scale = zero_<T>();
+      } else {
+        double nrm = sqrt(abs2_(alpha) + xn);
+        double beta = re_(alpha) >= 0.0 ? -nrm : nrm;
+        T bt = from_re<T>(beta);
+        sh_tau = div_(bt - alpha, bt);
+        sh_beta = bt;
+        sh_scale = div_(from_re<T>(1.0), alpha - bt);
+      }
+      sh_trivial = trivial;
+    }
+    __syncthreads();
+    const T tau = sh_tau;
+    if (sh_trivial) {
+      if (blk == 0 && tid < b) Tm[tid + c * b] = zero_<T>();
+      continue;  // uniform over the grid: every block computed the same reflector
+    }
+    const T scale = sh_scale;
+    for (int r = max(0, c + 1 - lo) + tid; r < rows; r += NT) base[r + c * ld] = scale * base[r + c * ld];
+    if (tid == 0 && lo <= c && c < hi) base[(c - lo) + c * ld] = sh_beta;
+    __syncthreads();
+    // ---- partial inner products: w_j = v^H P(:, j) (j > c), s_j = Y(:, j)^H v (j < c)
+    {
+      T acc = zero_<T>();
+      if (grp < NG && jj != c) {
+        for (int r = max(0, c - lo) + grp; r < rows; r += NG) {
+          const T vr = (lo + r == c) ? from_re<T>(1.0) : base[r + c * ld];
+          const T x = base[r + jj * ld];
+          acc += (jj > c) ? cmul(vr, x) : cmul(x, vr);
+        }
+      }
+      red2[tid] = acc;
+      __syncthreads();
+      if (tid < b) {
+        T sum = zero_<T>();
+        for (int g = 0; g < NG; ++g) sum += red2[g * b + tid];
+        w_part[(long long)blk * b + tid] = sum;
+      }
+    }
+    if (!grid_sync(gb, 102)) return;
+    // ---- C: apply H^H to the remaining columns; column c of T (block 0)
+    if (tid < b) {
+      T sum = zero_<T>();
+      for (int q = 0; q < (int)gridDim.x; ++q) sum += ldcg_(&w_part[(long long)q * b + tid]);
+      wv[tid] = sum;
+    }
+    __syncthreads();
+    const T ctau = conj_(tau);
+    if (grp < NG && jj > c) {
+      const T wj = ctau * wv[jj];
+      for (int r = max(0, c - lo) + grp; r < rows; r += NG) {
+        const T vr = (lo + r == c) ? from_re<T>(1.0) : base[r + c * ld];
+        base[r + jj * ld] -= vr * wj;
+      }
+    }
+    if (blk == 0 && tid < b) {
+      T val = zero_<T>();
+      if (tid < c) {
+        T acc = zero_<T>();
+        for (int l = tid; l < c; ++l) acc += Tm[tid + l * b] * wv[l];
+        val = -(tau * acc);
+      } else if (tid == c) {
+        val = tau;
+      }
+      Tm[tid + c * b] = val;
+    }
+    __syncthreads();
+  }
+  // ---- write back: R (upper part) into the panel with zeros below, Y explicitly
+  for (int idx = tid; idx < rows * b; idx += NT) {
+    const int r = idx % rows, j = idx / rows;
+    const int pr = lo + r;
+    const T val = base[r + j * ld];
+    Y[pr + j * ldy] = (pr == j) ? from_re<T>(1.0) : (pr > j ? val : zero_<T>());
+    P[pr + j * ldp] = (pr <= j) ? val : zero_<T>();
+  }
+}
+
+// band[(i-j) + j*ldb] = A(i,j) for 0 <= i-j <= b, zero for b < i-j < ldb.
+template <class T>
+__global__ void k_extract_band(int n, int b, const T* A, long long lda, T* band, int ldb) {
+  const long long total = (long long)n * ldb;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int d = (int)(t % ldb), j = (int)(t / ldb);
+    const int i = j + d;
+    T v = zero_<T>();
+    if (d <= b && i < n) v = A[i + j * lda];
+    if (d == 0) v = from_re<T>(re_(v));
+    band[t] = v;
+  }
+}
+
+template <class T> size_t panel_smem(int R, int b, int use_smem) {
+  size_t s = (size_t)(NT + b) * sizeof(T) + 32 * sizeof(double) + 64;
+  if (use_smem) s += (size_t)(R | 1) * b * sizeof(T);
+  return s;
+}
+
+}  // namespace
+
+template <class T> int he2hb(Sys& s, T* A, int lda, int b) {
+  const int n = s.n;
+  static bool attr = false;
+  if (!attr) {
+    GEV_CUDA_TRY(cudaFuncSetAttribute(k_panel_qr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      227 * 1024));
+    attr = true;
+  }
+  T* V1 = (T*)s.V1;
+  T* T1 = (T*)s.T1;
+  T* W0 = (T*)s.Pn;
+  T* W1 = W0 + (size_t)n * 2 * s.b;
+  T* sm0 = (T*)s.small;
+  T* sm1 = sm0 + (size_t)s.b * s.b;
+  double* nrm_part = (double*)s.panelws;
+  T* alpha_g = (T*)(nrm_part + 4096);
+  T* w_part = alpha_g + 2;
+  GridBar gb{(unsigned*)&s.status[ST_BARRIER_CNT], (unsigned*)&s.status[ST_BARRIER_GEN], s.status,
+             &s.status[ST_ABORT]};
+  const T one = from_re<T>(1.0), mone = from_re<T>(-1.0), zero = zero_<T>(), mhalf = from_re<T>(-0.5);
+  int npanel = 0;
+  for (int j0 = 0;; j0 += b) {
+    const int r0 = j0 + b;
+    const int m = n - r0;
+    if (m < 2) break;
+    ++npanel;
+    T* Pp = A + r0 + (long long)j0 * lda;
+    T* Yp = V1 + r0 + (long long)j0 * n;
+    T* Tp = T1 + (long long)j0 * b;
+    // ---- launch geometry: rows per block, shared-memory residency when it fits
+    int per_sm = 1;
+    int G = s.sms;
+    int R = (m + G - 1) / G;
+    if (R < 16) R = 16;
+    G = (m + R - 1) / R;
+    int use_smem = panel_smem<T>(R, b, 1) <= (size_t)200 * 1024 ? 1 : 0;
+    size_t smem = panel_smem<T>(R, b, use_smem);
+    GEV_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_panel_qr<T>, NT, smem));
+    if (per_sm < 1 || G > per_sm * s.sms) return GEV_ERR_UNSUPPORTED;
+    if (G > 4096) return GEV_ERR_UNSUPPORTED;
+    GEV_CUDA_TRY(cudaMemsetAsync(&s.status[ST_BARRIER_CNT], 0, 2 * sizeof(int), s.stream));
+    int mm = m, bb = b;
+    long long ldp = lda, ldy = n;
+    void* args[] = {&mm, &bb, &Pp, &ldp, &Yp, &ldy, &Tp, &nrm_part, &w_part, &alpha_g, &gb, &R, &use_smem};
+    GEV_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_panel_qr<T>, dim3(G), dim3(NT), args, smem, s.stream));
+    // ---- two-sided update of the trailing block
+    T* A22 = A + r0 + (long long)r0 * lda;
+    gemm(s, gp<T>(m, b, m, 0, 0, one, A22, lda, Yp, n, zero, W0, n));  // W0 = A22 Y
+    GemmP<T> g = gp<T>(m, b, b, 0, 0, one, W0, n, Tp, b, zero, W1, n);   // W = W0 T
+    g.tri_b = 2;
+    gemm(s, g);
+    gemm(s, gp<T>(b, b, m, 2, 0, one, Yp, n, W1, n, zero, sm0, b));    // Z = Y^H W
+    g = gp<T>(b, b, b, 2, 0, one, Tp, b, sm0, b, zero, sm1, b);         // U = T^H Z
+    g.tri_a = 1;
+    gemm(s, g);
+    gemm(s, gp<T>(m, b, b, 0, 0, mhalf, Yp, n, sm1, b, one, W1, n));   // V = W - Y U / 2
+    g = gp<T>(m, m, b, 0, 2, mone, Yp, n, W1, n, one, A22, lda);        // A22 -= Y V^H
+    g.c_lower = 1;
+    gemm(s, g);
+    g = gp<T>(m, m, b, 0, 2, mone, W1, n, Yp, n, one, A22, lda);        // A22 -= V Y^H
+    g.c_lower = 1;
+    gemm(s, g);
+    GEV_TRY(mirror_lower<T>(s, m, A22, lda));
+  }
+  // ---- compact band for the bulge chasing
+  const int ldb = 2 * b;
+  if (ldb > s.ldband) return GEV_ERR_UNSUPPORTED;
+  {
+    long long total = (long long)n * ldb;
+    unsigned blocks = cdiv(total, 256);
+    if (blocks > 16u * s.sms) blocks = 16u * s.sms;
+    k_extract_band<T><<<blocks, 256, 0, s.stream>>>(n, b, A, lda, (T*)s.band, ldb);
+    GEV_TRY(last_error());
+  }
+  s.band_b_used = b;
+  s.have_band = true;
+  s.have_tridiag_refl = false;
+  s.nsbr_panels = npanel;
+  return 0;
+}
+
+// Y <- Q1 Y (n x k): apply the panels' compact-WY blocks, last panel first.
+template <class T> int bt_he2hb(Sys& s, T* Yb, int ldy, int k) {
+  const int n = s.n, b = s.band_b_used;
+  T* V1 = (T*)s.V1;
+  T* T1 = (T*)s.T1;
+  T* Wk = (T*)s.Pn;                       // b x k
+  T* Wk2 = Wk + (size_t)n * 2 * s.b;      // b x k
+  const T one = from_re<T>(1.0), mone = from_re<T>(-1.0), zero = zero_<T>();
+  for (int p = s.nsbr_panels - 1; p >= 0; --p) {
+    const int j0 = p * b, r0 = j0 + b, m = n - r0;
+    const T* Yp = V1 + r0 + (long long)j0 * n;
+    const T* Tp = T1 + (long long)j0 * b;
+    T* Ysub = Yb + r0;
+    gemm(s, gp<T>(b, k, m, 2, 0, one, Yp, n, Ysub, ldy, zero, Wk, b));
+    GemmP<T> g = gp<T>(b, k, b, 0, 0, one, Tp, b, Wk, b, zero, Wk2, b);
+    g.tri_a = 2;
+    gemm(s, g);
+    gemm(s, gp<T>(m, k, b, 0, 0, mone, Yp, n, Wk2, b, one, Ysub, ldy));
+  }
+  return last_error();
+}
+
+// Step 6 ("Back"): Y = Q1 Q2 D Z.
+template <class T> int back(Sys& s, const double* Z, int ldz, int k, T* Y, int ldy) {
+  GEV_TRY(bt_hb2st<T>(s, Z, ldz, k, Y, ldy));
+  GEV_TRY(bt_he2hb<T>(s, Y, ldy, k));
+  return 0;
+}
+
+template int back<double>(Sys&, const double*, int, int, double*, int);
+template int back<zd>(Sys&, const double*, int, int, zd*, int);
+template int he2hb<double>(Sys&, double*, int, int);
+template int he2hb<zd>(Sys&, zd*, int, int);
+template int bt_he2hb<double>(Sys&, double*, int, int);
+template int bt_he2hb<zd>(Sys&, zd*, int, int);
+
+}  // namespace gev

@@ -1,0 +1,276 @@
+"""Thin Python binding of the C ABI in ``include/gev.h`` / ``include/gev_steps.h``.
+
+Argument marshalling only: every step of the solve runs in the CUDA kernels of ``libgev.so``.
+PyTorch supplies device memory and the stream.  There is no CPU fallback: if the library is not
+built, or no CUDA device is present, the calls raise.
+
+Layout convention.  The library works on column-major matrices.  A column-major ``rows x cols``
+matrix M is held here as a contiguous torch tensor of shape ``(cols, rows)`` (the row-major buffer
+of M^T); ``cm(M)`` makes one from a logical tensor and ``logical(B)`` views it back.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libgev.so")
+
+GEV_F64, GEV_C128 = 0, 1
+GEV_PLAIN, GEV_MIXED = 0, 1
+ERRORS = {
+    1: "GEV_ERR_NOT_SPD", 2: "GEV_ERR_NO_CONVERGENCE", 3: "GEV_ERR_TIMEOUT", 4: "GEV_ERR_OOM",
+    5: "GEV_ERR_CUDA", 6: "GEV_ERR_REUSE_WITHOUT_FACTOR", 7: "GEV_ERR_UNSUPPORTED",
+}
+STEP_NAMES = ["cholesky", "invert", "multiply", "to_band", "to_tridiag", "solve", "back_tridiag",
+              "back_band", "mult", "refine"]
+NSTEPS = len(STEP_NAMES)
+
+SYMBOLS = [
+    "gev_default_opts", "gev_setup", "gev_solve", "gev_reuse_factor", "gev_free",
+    "gev_workspace_bytes", "gev_strerror", "gev_step_potrf", "gev_step_trtri", "gev_step_hegst",
+    "gev_step_he2hb", "gev_step_hb2st", "gev_step_stedc", "gev_step_back", "gev_step_mult",
+]
+
+
+class GevError(RuntimeError):
+    def __init__(self, code: int, where: str, info: int = 0):
+        name = ERRORS.get(code, "invalid argument %d" % (-code) if code < 0 else f"error {code}")
+        super().__init__(f"{where}: {name}" + (f" (info={info})" if info else ""))
+        self.code = code
+        self.info = info
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("prec", ctypes.c_int),
+                ("band_b", ctypes.c_int), ("panel_nb", ctypes.c_int), ("refine_tol", ctypes.c_double),
+                ("refine_max_iter", ctypes.c_int), ("workspace_limit", ctypes.c_size_t),
+                ("timing", ctypes.c_int)]
+
+
+class Report(ctypes.Structure):
+    _fields_ = [("info", ctypes.c_int), ("deflated", ctypes.c_int), ("refine_iters", ctypes.c_int),
+                ("reused_factor", ctypes.c_int), ("refine_resid", ctypes.c_double),
+                ("ms", ctypes.c_double * NSTEPS), ("workspace_bytes", ctypes.c_size_t)]
+
+    def as_dict(self):
+        return {"info": self.info, "deflated": self.deflated, "refine_iters": self.refine_iters,
+                "reused_factor": self.reused_factor, "refine_resid": self.refine_resid,
+                "ms": dict(zip(STEP_NAMES, list(self.ms))), "workspace_bytes": self.workspace_bytes}
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libgev.so (built by ``paper_2502_02460_gb300.build.build()``); raise if missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built; run paper_2502_02460_gb300.build.build() "
+                               "(the solver has no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        ip = ctypes.POINTER(ctypes.c_int)
+        L.gev_default_opts.argtypes = [ctypes.POINTER(Opts)]
+        L.gev_default_opts.restype = None
+        L.gev_setup.argtypes = [ctypes.POINTER(vp), i, i, ctypes.POINTER(Opts)]
+        L.gev_solve.argtypes = [vp, vp, i, vp, i, i, vp, vp, i, ctypes.POINTER(Report)]
+        L.gev_reuse_factor.argtypes = [vp, i]
+        L.gev_free.argtypes = [vp]
+        L.gev_workspace_bytes.argtypes = [i, i, ctypes.POINTER(Opts)]
+        L.gev_workspace_bytes.restype = ctypes.c_size_t
+        L.gev_strerror.argtypes = [i]
+        L.gev_strerror.restype = ctypes.c_char_p
+        L.gev_step_potrf.argtypes = [vp, vp, i, ip]
+        L.gev_step_trtri.argtypes = [vp, vp, i]
+        L.gev_step_hegst.argtypes = [vp, vp, i, vp, i, vp, i]
+        L.gev_step_he2hb.argtypes = [vp, vp, i, i, ip]
+        L.gev_step_hb2st.argtypes = [vp, vp, vp]
+        L.gev_step_stedc.argtypes = [vp, vp, vp, i, vp, vp, i, ip]
+        L.gev_step_back.argtypes = [vp, vp, i, i, vp, i]
+        L.gev_step_mult.argtypes = [vp, vp, i, vp, i, i, vp, i]
+        for s in SYMBOLS:
+            getattr(L, s).restype = getattr(L, s).restype or ctypes.c_int
+        _lib = L
+    return _lib
+
+
+# ------------------------------------------------------------------------------ layout helpers --
+def cm(M):
+    """Column-major buffer of a logical torch matrix (shape (cols, rows), contiguous)."""
+    return M.transpose(0, 1).contiguous()
+
+
+def logical(B):
+    """Logical matrix view of a column-major buffer."""
+    return B.transpose(0, 1)
+
+
+def cm_from_numpy(M: np.ndarray, device):
+    """Column-major device buffer from a numpy matrix."""
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(np.asarray(M).T)).to(device)
+
+
+def numpy_from_cm(B) -> np.ndarray:
+    """numpy (Fortran-ordered) matrix from a column-major device buffer."""
+    return B.detach().cpu().numpy().T
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _check(code: int, where: str, info: int = 0):
+    if code != 0:
+        raise GevError(code, where, info)
+
+
+# ------------------------------------------------------------------------------------- handle --
+class Solver:
+    """One handle (``gev_setup``) for problems of order n: workspace, resident factor, stream."""
+
+    def __init__(self, n: int, complex_: bool = False, device=None, mixed: bool = False,
+                 band_b: int = 0, panel_nb: int = 0, timing: bool = False, stream=None,
+                 workspace_limit: int = 0, refine_tol: float = 0.0, refine_max_iter: int = 0):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("the solver needs a CUDA device (no CPU fallback)")
+        self.device = torch.device(device if device is not None else "cuda")
+        if self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        self.n = n
+        self.complex = complex_
+        self.dtype = torch.complex128 if complex_ else torch.float64
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        o = Opts()
+        lib().gev_default_opts(ctypes.byref(o))
+        o.device = self.device.index
+        o.cuda_stream = ctypes.c_void_p(self.stream.cuda_stream)
+        o.prec = GEV_MIXED if mixed else GEV_PLAIN
+        o.band_b = band_b
+        o.panel_nb = panel_nb
+        o.timing = 1 if timing else 0
+        o.workspace_limit = workspace_limit
+        o.refine_tol = refine_tol
+        o.refine_max_iter = refine_max_iter
+        self.opts = o
+        h = ctypes.c_void_p()
+        _check(lib().gev_setup(ctypes.byref(h), n, GEV_C128 if complex_ else GEV_F64, ctypes.byref(o)),
+               "gev_setup")
+        self.h = h
+        self.last_report = None
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().gev_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def reuse_factor(self, enable: bool = True):
+        _check(lib().gev_reuse_factor(self.h, 1 if enable else 0), "gev_reuse_factor")
+
+    def _empty(self, rows, cols, dtype=None):
+        import torch
+
+        return torch.empty((cols, rows), dtype=dtype or self.dtype, device=self.device)
+
+    # full solve on column-major buffers ------------------------------------------------------
+    def solve_cm(self, Hb, Sb, k: int, evals=None, Cb=None):
+        """H, S: column-major buffers (S may be None after ``reuse_factor(True)``)."""
+        import torch
+
+        n = self.n
+        if evals is None:
+            evals = torch.empty(k, dtype=torch.float64, device=self.device)
+        if Cb is None:
+            Cb = self._empty(n, k)
+        rep = Report()
+        code = lib().gev_solve(self.h, _ptr(Hb), n, _ptr(Sb), n, k, _ptr(evals), _ptr(Cb), n,
+                               ctypes.byref(rep))
+        self.last_report = rep.as_dict()
+        _check(code, "gev_solve", rep.info)
+        return evals, Cb
+
+    def solve(self, H, S, k: int):
+        """Logical torch matrices (n x n) in, (eigenvalues[k], C[n x k]) out."""
+        Hb = cm(H.to(self.device, self.dtype))
+        Sb = cm(S.to(self.device, self.dtype)) if S is not None else None
+        w, Cb = self.solve_cm(Hb, Sb, k)
+        return w, logical(Cb)
+
+    # individual steps (include/gev_steps.h) --------------------------------------------------
+    def potrf(self, Ab):
+        info = ctypes.c_int(0)
+        code = lib().gev_step_potrf(self.h, _ptr(Ab), self.n, ctypes.byref(info))
+        if code not in (0, 1):
+            _check(code, "gev_step_potrf")
+        return info.value
+
+    def trtri(self, Ab):
+        _check(lib().gev_step_trtri(self.h, _ptr(Ab), self.n), "gev_step_trtri")
+
+    def hegst(self, Hb, Xb, Ab=None):
+        if Ab is None:
+            Ab = self._empty(self.n, self.n)
+        _check(lib().gev_step_hegst(self.h, _ptr(Hb), self.n, _ptr(Xb), self.n, _ptr(Ab), self.n),
+               "gev_step_hegst")
+        return Ab
+
+    def he2hb(self, Ab, b: int = 0) -> int:
+        used = ctypes.c_int(0)
+        _check(lib().gev_step_he2hb(self.h, _ptr(Ab), self.n, b, ctypes.byref(used)), "gev_step_he2hb")
+        return used.value
+
+    def hb2st(self):
+        import torch
+
+        d = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        e = torch.empty(max(self.n - 1, 1), dtype=torch.float64, device=self.device)
+        _check(lib().gev_step_hb2st(self.h, _ptr(d), _ptr(e)), "gev_step_hb2st")
+        return d, e[: self.n - 1]
+
+    def stedc(self, d, e, k: int):
+        import torch
+
+        n = self.n
+        w = torch.empty(n, dtype=torch.float64, device=self.device)
+        Zb = self._empty(n, k, torch.float64)
+        ee = e if e.numel() > 0 else torch.zeros(1, dtype=torch.float64, device=self.device)
+        defl = ctypes.c_int(0)
+        _check(lib().gev_step_stedc(self.h, _ptr(d), _ptr(ee), k, _ptr(w), _ptr(Zb), n,
+                                    ctypes.byref(defl)), "gev_step_stedc")
+        return w, Zb, defl.value
+
+    def back(self, Zb, k: int):
+        Yb = self._empty(self.n, k)
+        _check(lib().gev_step_back(self.h, _ptr(Zb), self.n, k, _ptr(Yb), self.n), "gev_step_back")
+        return Yb
+
+    def mult(self, Xb, Yb, k: int):
+        Cb = self._empty(self.n, k)
+        _check(lib().gev_step_mult(self.h, _ptr(Xb), self.n, _ptr(Yb), self.n, k, _ptr(Cb), self.n),
+               "gev_step_mult")
+        return Cb
+
+
+def solve(H, S, k: int, **kw):
+    """One-shot generalized solve: the k lowest eigenpairs of the pencil (H, S) (torch, on GPU)."""
+    with Solver(H.shape[0], complex_=H.is_complex(), device=H.device, **kw) as s:
+        return s.solve(H, S, k)
