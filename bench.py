@@ -1,0 +1,292 @@
+"""Benchmark: time-to-solution of the dense generalized Hermitian eigensolve H C = S C Lambda.
+
+Workload (default): the N=16384 real configuration (k = 4096 lowest eigenpairs, seed 3, Toeplitz
+overlap and DFT-like spectrum; see paper_2502_02460_gb300/inputs.py).  A step is one complete
+gev_solve (Cholesky, inversion, Multiply, full->band, bulge chasing, divide and conquer, both
+back-transforms, C = X^H Y) on inputs already resident in HBM.  H and S are 2 x 2.1 GB, far larger
+than L2 (129 MB), so no L2 flush is needed between steps.
+
+Printed (rank 0, one JSON line): seconds per solve (lower is better), the roofline entry of the
+dominant kernel (the FP64 DMMA GEMM: algorithmic flops of every launch / CUDA-event time of every
+launch, on the solve stream), the CPU oracle on a bounded sample, the end-to-end time through the
+Python API with pinned host buffers, the number of kernels launched, SM clocks sampled during the
+timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--n N --k K] [--impl reference]
+
+Multi-GPU (torchrun, one rank per GPU): every rank solves its own independent system (k-points /
+spin channels are independent problems), no collective on the data path; value = solves of all
+ranks / max-over-ranks time ("weak" scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "N=16384 gen. eigensolve s (FP64 vs mixed, resid≤1e-11); k-pt stream p50/p99 ms"
+FP64_NOMINAL_TF = 1.25      # GB300 FP64 (DMMA) nominal, dense
+BF16_NOMINAL_TF = 2250.0    # GB300 BF16 nominal, dense
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            mp = json.load(f)
+        return mp, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax = float(parts[2])
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(n_full: int, k_full: int, complex_: bool, seconds_target: float = 15.0):
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the same recipe, scaled to the
+    metric's unit (seconds per N=n_full solve) by the cubic cost of the dense solve."""
+    import numpy as np
+
+    import oracle
+    from paper_2502_02460_gb300 import inputs
+
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    ns = 512
+    t = 0.0
+    while True:
+        p = inputs.make_problem(ns, max(1, ns * k_full // n_full), seed=3, complex_=complex_)
+        t0 = time.perf_counter()
+        w, C, info, dg = oracle.gev(p.H, p.S, max(1, ns * k_full // n_full))
+        t = time.perf_counter() - t0
+        if t >= seconds_target / 8 or ns >= 2048:
+            break
+        ns *= 2
+    scaled = t * (n_full / ns) ** 3
+    return {"value": scaled, "unit": "s", "cores": int(os.environ.get("OMP_NUM_THREADS", cores)),
+            "kind": "oracle",
+            "sample": f"oracle on N={ns}, k={max(1, ns * k_full // n_full)} of the same recipe "
+                      f"({t:.2f} s), scaled by (N/{ns})^3 to N={n_full}"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    cores = os.cpu_count() or 1
+    vals = []
+    sample = None
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(args.n, args.k, args.complex, seconds_target=4.0)
+        if i >= args.warmup:
+            vals.append(cb["value"])
+        sample = cb["sample"]
+    v = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(args),
+            "cpu_baseline": {"kind": "oracle", "cores": cores, "sample": sample, "value": v, "unit": "s"},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(args):
+    return {"workload": f"{'complex128' if args.complex else 'real'} N={args.n}, k={args.k} lowest "
+                        f"eigenpairs, seed {args.seed}, Toeplitz S, DFT-like spectrum; "
+                        f"{'mixed' if args.mixed else 'plain FP64'} path",
+            "n": args.n, "k": args.k, "precision": "mixed" if args.mixed else "plain",
+            "band_b": args.band_b, "l2": "inputs (2 x n^2 x 8 B) larger than L2; no flush needed"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--n", type=int, default=16384)
+    ap.add_argument("--k", type=int, default=4096)
+    ap.add_argument("--seed", type=int, default=3)
+    ap.add_argument("--complex", action="store_true")
+    ap.add_argument("--mixed", action="store_true")
+    ap.add_argument("--band-b", type=int, default=32)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    from paper_2502_02460_gb300 import build, gev, inputs
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    if rank == 0:
+        build.build()
+    if ws > 1:
+        torch.distributed.barrier()
+    # independent system per rank (weak scaling): seed offset by rank
+    p = inputs.make_problem(args.n, args.k, seed=args.seed + 100 * rank, complex_=args.complex,
+                            device=dev, gap_check=False)
+    Hb, Sb = p.H, p.S  # column-major device buffers
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    solver = gev.Solver(args.n, complex_=args.complex, device=dev, mixed=args.mixed,
+                        band_b=args.band_b, timing=2, stream=stream)
+    w = torch.empty(args.k, dtype=torch.float64, device=dev)
+    Cb = torch.empty((args.k, args.n), dtype=solver.dtype, device=dev)
+    for _ in range(args.warmup):
+        solver.solve_cm(Hb, Sb, args.k, w, Cb)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    reps = []
+    e0.record(stream)
+    for _ in range(args.steps):
+        solver.solve_cm(Hb, Sb, args.k, w, Cb)
+        reps.append(solver.last_report)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    # accuracy of the benchmarked result against the construction (exact eigenvalues)
+    wl = w.cpu().numpy()
+    import numpy as np
+
+    err = float(np.max(np.abs(wl - p.lam[: args.k])))
+    # roofline of the dominant kernel: FP64 DMMA GEMM
+    gemm_ms = sum(r["gemm_ms"] for r in reps)
+    gemm_fl = sum(r["gemm_flops"] for r in reps)
+    gemm_calls = sum(r["gemm_calls"] for r in reps)
+    mp, src = peaks()
+    fp64_peak = mp.get("bf16_tflops_sustained", 1764.7) * FP64_NOMINAL_TF / BF16_NOMINAL_TF
+    achieved = gemm_fl / (gemm_ms * 1e-3) / 1e12 if gemm_ms > 0 else None
+    step_ms = {k: statistics.median(r["ms"][k] for r in reps) for k in gev.STEP_NAMES}
+    launches = int(statistics.median(r["launches"] for r in reps))
+    # end-to-end through the Python API with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        Hh = Hb.cpu().pin_memory()
+        Sh = Sb.cpu().pin_memory()
+        wh = torch.empty(args.k, dtype=torch.float64).pin_memory()
+        Ch = torch.empty((args.k, args.n), dtype=solver.dtype).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Hd = Hh.to(dev, non_blocking=True)
+        Sd = Sh.to(dev, non_blocking=True)
+        wd, Cd = solver.solve_cm(Hd, Sd, args.k)
+        wh.copy_(wd, non_blocking=True)
+        Ch.copy_(Cd, non_blocking=True)
+        torch.cuda.synchronize()
+        t_e2e = time.perf_counter() - t0
+        es = 16 if args.complex else 8
+        e2e = {"value": t_e2e, "unit": "s", "h2d_bytes_per_step": 2 * args.n * args.n * es,
+               "d2h_bytes_per_step": args.k * 8 + args.n * args.k * es}
+        del Hd, Sd
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.barrier()
+        return 0
+    cb = None if args.no_cpu_baseline else cpu_baseline(args.n, args.k, args.complex)
+    value = ms / 1e3 / (1 if ws == 1 else 1)  # seconds per solve (each rank solves one system)
+    line = {
+        "metric": METRIC, "value": value, "unit": "s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(args),
+        "solves_per_s": ws / (ms / 1e3),
+        "max_abs_eig_err_vs_construction": err,
+        "steps_ms": step_ms,
+        "roofline": {"bound": "tensor", "kernel": "gemm_kernel<double> (FP64 DMMA mma.sync m8n8k4)",
+                     "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                     "frac": (achieved / fp64_peak) if achieved else None, "traffic": None,
+                     "launches_timed": gemm_calls,
+                     "peak_source": f"{src} bf16 sustained x FP64/BF16 nominal ratio "
+                                    f"({FP64_NOMINAL_TF}/{BF16_NOMINAL_TF})"},
+        "cpu_baseline": cb, "e2e": e2e, "gpu_launches": launches * args.steps, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.barrier()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -78,7 +78,8 @@ typedef struct {
   double refine_tol;     /* mixed form: target residual (0 = 1e-11) */
   int refine_max_iter;   /* mixed form: refinement iteration cap (0 = 4) */
   size_t workspace_limit;/* bytes; 0 = no limit */
-  int timing;            /* non-zero: record per-step times into gev_report.ms */
+  int timing;            /* 1: record per-step times into gev_report.ms; 2: also time every GEMM
+                            launch (CUDA events) and sum its algorithmic flops (gemm_ms/gemm_flops) */
 } gev_opts;
 
 typedef struct {
@@ -89,6 +90,10 @@ typedef struct {
   double refine_resid;      /* mixed form: last refinement residual ||A Y - Y L||_1/(||A||_1) */
   double ms[GEV_NSTEPS];    /* per-step times when opts.timing != 0 */
   size_t workspace_bytes;   /* device bytes held by the handle */
+  long long launches;       /* kernels launched by the last call */
+  int gemm_calls;           /* timing == 2: GEMM launches timed */
+  double gemm_ms;           /* timing == 2: summed GEMM durations (ms, CUDA events) */
+  double gemm_flops;        /* timing == 2: summed algorithmic GEMM flops (triangles excluded) */
 } gev_report;
 
 /* Fill *opts with the defaults (device 0, default stream, GEV_PLAIN, automatic sizes). */

@@ -248,67 +248,57 @@ __global__ void k_phase_rows(int n, int k, const double* Z, long long ldz, const
   }
 }
 
-// Y <- Q2 Y.  Block = one thread per column of a BNc-wide column block.  Reflectors are applied in
-// groups of G consecutive sweeps (last group first); inside a group, for t = 0, 1, ... the rows
-// touched by H(s0..s0+G-1, t) form a window of b+G-1 rows, staged in shared memory, to which the
-// group's reflectors are applied in the order s = s0+G-1 .. s0.  (Within a sweep the reflectors act
-// on disjoint rows and commute; H(s',t') with s' > s must stay to the right of H(s,t) only for
-// t' in {t-1, t}; the order "t ascending, s descending" respects that.)
-template <class T>
-__global__ void k_bt_bulge(int n, int k, int b, int G, const T* V2, const T* tau2, int ntask, T* Y,
-                           long long ldy) {
+// Y <- Q2 Y, level-parallel.  With G = b sweeps per group, the block D_t^g of group g
+// (reflectors H(s, t), s = gb .. gb+b-1, applied in the order s descending) acts on the row window
+// [(g+t) b + 1, (g+t+2) b - 1).  Q2 = P_0 P_1 ... with P_g = D_T^g ... D_1^g D_0^g, so Y <- Q2 Y
+// applies D_0^last first.  D_t^g must follow D_{t-1}^g and D_{t'}^{g+1} for t' <= t (overlapping
+// windows), which is exactly the order of the levels L = t + (ngroups - 1 - g); blocks of one level
+// have windows 2b apart, act on disjoint rows and commute.  One launch per level: blockIdx.x picks
+// the group, blockIdx.y a block of columns of Y, one thread per column (all FMAs of a thread are
+// on its own column; the reflector entries are shared-memory broadcasts).
+template <class T, int COLS>
+__global__ void __launch_bounds__(COLS) k_bt_bulge_level(int n, int k, int b, int L, int ngroups,
+                                                         const T* V2, const T* tau2, int ntask, T* Y,
+                                                         long long ldy) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int BNc = blockDim.x;
-  const int c0 = blockIdx.x * BNc;
-  const int c = threadIdx.x;
-  const int LDZ = BNc + 1;
-  const int WR = b + G - 1;
-  T* Zw = reinterpret_cast<T*>(smraw);          // WR x BNc (row-major, padded)
-  T* Vs = Zw + (size_t)WR * LDZ;                 // G x b
-  T* ts = Vs + (size_t)G * b;                    // G
-  const int ncols = min(BNc, k - c0);
+  const int g = max(0, ngroups - 1 - L) + blockIdx.x;
+  const int t = L - (ngroups - 1 - g);
+  if (g >= ngroups || t < 0 || t >= ntask) return;
+  const int G = b;
+  const int s0 = g * G;
   const int last_sweep = n - 3;
-  if (last_sweep < 0) return;
-  const int ngroups = last_sweep / G + 1;
-  for (int g = ngroups - 1; g >= 0; --g) {
-    const int s0 = g * G;
-    const int s1 = min(s0 + G - 1, last_sweep);
-    for (int t = 0; t < ntask; ++t) {
-      const int w0 = s0 + 1 + t * b;
-      if (w0 >= n) break;
-      const int w1 = min(n, s1 + 1 + t * b + b);
-      const int rows = w1 - w0;
-      __syncthreads();
-      for (int idx = threadIdx.x; idx < rows * ncols; idx += BNc) {
-        const int r = idx % rows, cc = idx / rows;
-        Zw[r * LDZ + cc] = Y[(w0 + r) + (long long)(c0 + cc) * ldy];
-      }
-      for (int idx = threadIdx.x; idx < (s1 - s0 + 1) * b; idx += BNc) {
-        const int q = idx / b, i = idx % b;
-        Vs[q * b + i] = V2[((long long)(s0 + q) * ntask + t) * b + i];
-      }
-      for (int q = threadIdx.x; q <= s1 - s0; q += BNc) ts[q] = tau2[(long long)(s0 + q) * ntask + t];
-      __syncthreads();
-      if (c < ncols) {
-        for (int q = s1 - s0; q >= 0; --q) {
-          const T tau = ts[q];
-          if (tau == zero_<T>()) continue;
-          const int p = s0 + q + 1 + t * b;
-          const int len = min(b, n - p);
-          const int off = p - w0;
-          const T* vq = Vs + q * b;
-          T acc = zero_<T>();
-          for (int i = 0; i < len; ++i) acc += cmul(vq[i], Zw[(off + i) * LDZ + c]);
-          acc = tau * acc;
-          for (int i = 0; i < len; ++i) Zw[(off + i) * LDZ + c] -= vq[i] * acc;
-        }
-      }
-      __syncthreads();
-      for (int idx = threadIdx.x; idx < rows * ncols; idx += BNc) {
-        const int r = idx % rows, cc = idx / rows;
-        Y[(w0 + r) + (long long)(c0 + cc) * ldy] = Zw[r * LDZ + cc];
-      }
+  const int s1 = min(s0 + G - 1, last_sweep);
+  const int w0 = s0 + 1 + t * b;
+  if (w0 >= n) return;
+  const int w1 = min(n, s1 + 1 + t * b + b);
+  const int rows = w1 - w0;
+  const int c = blockIdx.y * COLS + threadIdx.x;
+  T* Zw = reinterpret_cast<T*>(smraw);   // rows x COLS (row-major)
+  T* Vs = Zw + (size_t)(2 * b) * COLS;   // G x b
+  T* ts = Vs + (size_t)G * b;            // G
+  const int ncols = min(COLS, k - (int)blockIdx.y * COLS);
+  for (int idx = threadIdx.x; idx < (s1 - s0 + 1) * b; idx += COLS) {
+    const int q = idx / b, i = idx % b;
+    Vs[q * b + i] = V2[((long long)(s0 + q) * ntask + t) * b + i];
+  }
+  for (int q = threadIdx.x; q <= s1 - s0; q += COLS) ts[q] = tau2[(long long)(s0 + q) * ntask + t];
+  if (threadIdx.x < ncols)
+    for (int r = 0; r < rows; ++r) Zw[r * COLS + threadIdx.x] = Y[(w0 + r) + (long long)c * ldy];
+  __syncthreads();
+  if (threadIdx.x < ncols) {
+    for (int q = s1 - s0; q >= 0; --q) {
+      const T tau = ts[q];
+      if (tau == zero_<T>()) continue;
+      const int p = s0 + q + 1 + t * b;
+      const int len = min(b, n - p);
+      const int off = p - w0;
+      const T* vq = Vs + q * b;
+      T acc = zero_<T>();
+      for (int i = 0; i < len; ++i) acc += cmul(vq[i], Zw[(off + i) * COLS + threadIdx.x]);
+      acc = tau * acc;
+      for (int i = 0; i < len; ++i) Zw[(off + i) * COLS + threadIdx.x] -= vq[i] * acc;
     }
+    for (int r = 0; r < rows; ++r) Y[(w0 + r) + (long long)c * ldy] = Zw[r * COLS + threadIdx.x];
   }
 }
 
@@ -327,7 +317,7 @@ template <class T> int hb2st(Sys& s, double* d, double* e) {
     const size_t smem = bulge_smem<T>(b);
     static bool attr = false;
     if (!attr) {
-      GEV_CUDA_TRY(cudaFuncSetAttribute(k_bulge<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+      GEV_TRY(allow_max_dyn_smem(k_bulge<T>));
       attr = true;
     }
     int per_sm = 0;
@@ -345,13 +335,17 @@ template <class T> int hb2st(Sys& s, double* d, double* e) {
     int* st = s.status;
     int* ab = &s.status[ST_ABORT];
     void* args[] = {&nn, &bb, &band, &lb, &V2, &tau2, &nt, &prog, &st, &ab};
+    GEV_COUNT(s);
     GEV_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_bulge<T>, dim3(G), dim3(NT), args, smem, s.stream));
   }
+  GEV_COUNT(s);
   k_tridiag_out<T><<<1, 256, 0, s.stream>>>(n, band, ldb, d, e, (T*)s.phase);
   GEV_TRY(last_error());
   s.have_tridiag_refl = true;
   return 0;
 }
+
+template <class T, int COLS> int bt_levels(Sys& s, int n, int k, int b, T* Y, int ldy);
 
 // Y (n x k) = Q2 D Z for real Z.
 template <class T> int bt_hb2st(Sys& s, const double* Z, int ldz, int k, T* Y, int ldy) {
@@ -360,21 +354,38 @@ template <class T> int bt_hb2st(Sys& s, const double* Z, int ldz, int k, T* Y, i
     long long total = (long long)n * k;
     unsigned blocks = cdiv(total, 256);
     if (blocks > 16u * s.sms) blocks = 16u * s.sms;
+    GEV_COUNT(s);
     k_phase_rows<T><<<blocks, 256, 0, s.stream>>>(n, k, Z, ldz, (const T*)s.phase, Y, ldy);
     GEV_TRY(last_error());
   }
   if (n <= 2) return 0;
-  int BNc = 32;
-  while (BNc < 128 && cdiv(k, BNc * 2) >= (unsigned)s.sms) BNc *= 2;
+  // level-parallel application (see k_bt_bulge_level); one thread per column, as many columns
+  // per block as the staged window (2b rows) allows in shared memory
+  const size_t per_col = sizeof(T) * 2 * (size_t)b;
+  if (per_col * 256 <= (size_t)160 * 1024) return bt_levels<T, 256>(s, n, k, b, Y, ldy);
+  if (per_col * 128 <= (size_t)160 * 1024) return bt_levels<T, 128>(s, n, k, b, Y, ldy);
+  return bt_levels<T, 64>(s, n, k, b, Y, ldy);
+}
+
+template <class T, int COLS> int bt_levels(Sys& s, int n, int k, int b, T* Y, int ldy) {
   const int G = b;
-  const size_t smem = sizeof(T) * ((size_t)(b + G - 1) * (BNc + 1) + (size_t)G * b + G) + 64;
+  const int last_sweep = n - 3;
+  const int ngroups = last_sweep / G + 1;
+  const size_t smem = sizeof(T) * ((size_t)2 * b * COLS + (size_t)G * b + G) + 64;
   static bool attr = false;
   if (!attr) {
-    GEV_CUDA_TRY(cudaFuncSetAttribute(k_bt_bulge<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    GEV_TRY(allow_max_dyn_smem(k_bt_bulge_level<T, COLS>));
     attr = true;
   }
-  k_bt_bulge<T><<<cdiv(k, BNc), BNc, smem, s.stream>>>(n, k, b, G, (const T*)s.V2, (const T*)s.tau2,
-                                                        s.ntask, Y, ldy);
+  const int nlevels = ngroups + s.ntask;
+  const unsigned ycb = cdiv(k, COLS);
+  for (int L = 0; L < nlevels; ++L) {
+    const int gmin = ngroups - 1 - L > 0 ? ngroups - 1 - L : 0;
+    const int nblk = ngroups - gmin;
+    GEV_COUNT(s);
+    k_bt_bulge_level<T, COLS><<<dim3(nblk, ycb), COLS, smem, s.stream>>>(
+        n, k, b, L, ngroups, (const T*)s.V2, (const T*)s.tau2, s.ntask, Y, ldy);
+  }
   return last_error();
 }
 

@@ -123,6 +123,7 @@ template <class T> int potrf(Sys& s, T* A, int lda) {
   for (int j = 0; j < n; j += nb) {
     const int jb = nb < n - j ? nb : n - j;
     T* Ajj = A + j + (long long)j * lda;
+    GEV_COUNT(s);
     k_potrf_diag<T><<<1, 256, diag_smem<T>(), s.stream>>>(jb, Ajj, lda, Dinv, nb, s.status, j);
     GEV_TRY(last_error());
     const int m = n - j - jb;
@@ -143,31 +144,41 @@ template <class T> int potrf(Sys& s, T* A, int lda) {
   return last_error();
 }
 
+// In-place inverse of the lower-triangular block A[o:o+sz, o:o+sz] (o, sz multiples of nb except
+// at the end): X21 = -X22 (L21 X11) after inverting both diagonal halves, recursively, so the work
+// is done by a few large triangular GEMMs instead of a chain of thin ones.
+template <class T> void trtri_rec(Sys& s, T* A, int lda, int o, int sz, T* Dinv, T* W) {
+  const int nb = s.nb;
+  if (sz <= nb) {
+    copy2d<T>(s, sz, sz, Dinv + (long long)o * nb, nb, A + o + (long long)o * lda, lda);
+    return;
+  }
+  int n1 = (sz / 2 + nb - 1) / nb * nb;
+  if (n1 >= sz) n1 = sz - nb;
+  const int n2 = sz - n1;
+  trtri_rec(s, A, lda, o, n1, Dinv, W);
+  trtri_rec(s, A, lda, o + n1, n2, Dinv, W);
+  T* X11 = A + o + (long long)o * lda;
+  T* A21 = A + (o + n1) + (long long)o * lda;
+  T* X22 = A + (o + n1) + (long long)(o + n1) * lda;
+  const T one = from_re<T>(1.0), mone = from_re<T>(-1.0), zero = zero_<T>();
+  GemmP<T> g = gp<T>(n2, n1, n1, 0, 0, one, A21, lda, X11, lda, zero, W, s.n);  // W = L21 X11
+  g.tri_b = 1;
+  gemm(s, g);
+  g = gp<T>(n2, n1, n2, 0, 0, mone, X22, lda, W, s.n, zero, A21, lda);          // X21 = -X22 W
+  g.tri_a = 1;
+  gemm(s, g);
+}
+
 template <class T> int trtri(Sys& s, T* A, int lda) {
   const int n = s.n, nb = s.nb;
   GEV_TRY(set_smem_attrs<T>());
   T* Dinv = (T*)s.dinv;  // nb x n: all diagonal-block inverses
-  T* T1 = (T*)s.Pn;
-  const T one = from_re<T>(1.0), mone = from_re<T>(-1.0), zero = zero_<T>();
   const int nblk = (n + nb - 1) / nb;
+  GEV_COUNT(s);
   k_inv_diag_blocks<T><<<nblk, 256, diag_smem<T>(), s.stream>>>(n, nb, A, lda, Dinv);
   GEV_TRY(last_error());
-  for (int q = nblk - 1; q >= 0; --q) {
-    const int j = q * nb;
-    const int jb = nb < n - j ? nb : n - j;
-    const int m = n - j - jb;
-    if (m > 0) {
-      T* L21 = A + (j + jb) + (long long)j * lda;
-      T* X22 = A + (j + jb) + (long long)(j + jb) * lda;
-      GemmP<T> g = gp<T>(m, jb, m, 0, 0, one, X22, lda, L21, lda, zero, T1, n);
-      g.tri_a = 1;
-      gemm(s, g);
-      g = gp<T>(m, jb, jb, 0, 0, mone, T1, n, Dinv + (long long)j * nb, nb, zero, L21, lda);
-      g.tri_b = 1;
-      gemm(s, g);
-    }
-    GEV_TRY(copy2d<T>(s, jb, jb, Dinv + (long long)j * nb, nb, A + j + (long long)j * lda, lda));
-  }
+  trtri_rec<T>(s, A, lda, 0, n, Dinv, (T*)s.W1);
   GEV_TRY(zero_upper<T>(s, n, A, lda));
   return last_error();
 }

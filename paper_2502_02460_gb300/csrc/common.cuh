@@ -5,6 +5,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <cstdio>
+#include <vector>
 
 #include "gev.h"
 #include "gev_steps.h"
@@ -111,6 +112,7 @@ template <class T> struct GemmP {
 struct Sys;
 
 template <class T> void gemm(Sys& s, GemmP<T> p);
+void gemm_account(Sys& s, int* calls, double* ms, double* flops);
 template <class T> GemmP<T> gp(int M, int N, int K, int ta, int tb, T alpha, const T* A, long long lda,
                                const T* B, long long ldb, T beta, T* C, long long ldc) {
   GemmP<T> p{};
@@ -165,6 +167,13 @@ struct Sys {
   cudaEvent_t ev[GEV_NSTEPS + 1] = {};
   int* status_h = nullptr;  // pinned host mirror
 
+  // accounting of the current call
+  long long launches = 0;
+  bool account = false;                 // opts.timing == 2
+  std::vector<cudaEvent_t> gemm_ev;     // start/stop pairs
+  std::vector<double> gemm_fl;          // algorithmic flops per timed GEMM
+  int gemm_used = 0;
+
   bool have_factor = false;
   bool reuse = false;
   bool have_band = false;
@@ -200,7 +209,21 @@ inline int last_error() {
   return 0;
 }
 
+#define GEV_COUNT(s) (++(s).launches)
+
 inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
+
+// Raise a kernel's dynamic shared-memory limit to what the device allows beside its static use.
+template <class F> int allow_max_dyn_smem(F* func) {
+  int dev = 0, optin = 0;
+  GEV_CUDA_TRY(cudaGetDevice(&dev));
+  GEV_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  cudaFuncAttributes fa{};
+  GEV_CUDA_TRY(cudaFuncGetAttributes(&fa, (const void*)func));
+  GEV_CUDA_TRY(cudaFuncSetAttribute((const void*)func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    optin - (int)fa.sharedSizeBytes));
+  return 0;
+}
 
 // ---------------------------------------------------------------------------- step launchers --
 template <class T> int potrf(Sys& s, T* A, int lda);

@@ -587,11 +587,21 @@ int stedc(Sys& s, const double* d, const double* e, int k, double* w, double* Z,
   double* U = (double*)s.A;
   const long long ldq = n;
 
+  // Every column of a node must be zero outside the node's rows (block-diagonal eigenvector
+  // matrices): deflated columns are copied over the whole node range and Givens rotations mix full
+  // columns.  Both buffers are cleared here, so rows a level never writes stay zero.
+  GEV_CUDA_TRY(cudaMemsetAsync(Qa, 0, sizeof(double) * (size_t)n * n, st));
+  GEV_CUDA_TRY(cudaMemsetAsync(Qb, 0, sizeof(double) * (size_t)n * n, st));
   int nleaf = 1;
   while ((n + nleaf - 1) / nleaf > LEAF) nleaf *= 2;
   const unsigned eb = cdiv(n, 256) < 1024u ? cdiv(n, 256) : 1024u;
+  GEV_COUNT(s);
   k_tear<<<eb, 256, 0, st>>>(n, nleaf, d, e, A.dwork);
-  if (nleaf > 1) k_tear2<<<cdiv(nleaf, 256), 256, 0, st>>>(n, nleaf, e, A.dwork);
+  if (nleaf > 1) {
+    GEV_COUNT(s);
+    k_tear2<<<cdiv(nleaf, 256), 256, 0, st>>>(n, nleaf, e, A.dwork);
+  }
+  GEV_COUNT(s);
   k_leaf<<<nleaf, 64, 0, st>>>(n, nleaf, A.dwork, e, w, Qa, ldq, A.colmap, s.status);
   GEV_TRY(last_error());
 
@@ -607,6 +617,7 @@ int stedc(Sys& s, const double* d, const double* e, int k, double* w, double* Z,
       hn[q].c = (int)(((long long)(q + 1) * span * n) / nleaf);
     }
     GEV_CUDA_TRY(cudaMemcpyAsync(A.nodes, hn.data(), sizeof(Node) * nnodes, cudaMemcpyHostToDevice, st));
+    GEV_COUNT(s);
     k_merge_prep<<<nnodes, 1024, 0, st>>>(n, A.nodes, e, w, Qa, ldq, A);
     GEV_TRY(last_error());
     GEV_CUDA_TRY(cudaMemcpyAsync(hn.data(), A.nodes, sizeof(Node) * nnodes, cudaMemcpyDeviceToHost, st));
@@ -617,13 +628,17 @@ int stedc(Sys& s, const double* d, const double* e, int k, double* w, double* Z,
       Tmax = std::max(Tmax, x.K + x.ndefl);
     }
     if (Kmax > 0) {
+      GEV_COUNT(s);
       k_secular<<<dim3(cdiv(Kmax, 128), nnodes), 128, 0, st>>>(A.nodes, A, s.status);
+      GEV_COUNT(s);
       k_zprime<<<dim3(cdiv(Kmax, 128), nnodes), 128, 0, st>>>(A.nodes, A);
     }
     const int kcut = top ? k : 0x7fffffff;
+    GEV_COUNT(s);
     k_positions<<<dim3(cdiv(Tmax, 256), nnodes), 256, 0, st>>>(A.nodes, A, kcut, s.status);
     GEV_TRY(last_error());
     if (top) {
+      GEV_COUNT(s);
       k_count_out<<<nnodes, 32, 0, st>>>(A.nodes, A, kcut);
       GEV_CUDA_TRY(cudaMemcpyAsync(hn.data(), A.nodes, sizeof(Node) * nnodes, cudaMemcpyDeviceToHost, st));
       GEV_CUDA_TRY(cudaStreamSynchronize(st));
@@ -631,8 +646,14 @@ int stedc(Sys& s, const double* d, const double* e, int k, double* w, double* Z,
     }
     int Koutmax = 0;
     for (auto& x : hn) Koutmax = std::max(Koutmax, x.Kout);
-    if (Koutmax > 0) k_vectors<<<dim3(Koutmax, nnodes), 256, 0, st>>>(A.nodes, A, U, ldq);
-    if (Tmax > 0) k_gather<<<dim3(Tmax, nnodes), 256, 0, st>>>(A.nodes, A, Qa, ldq, Qg, Qb);
+    if (Koutmax > 0) {
+      GEV_COUNT(s);
+      k_vectors<<<dim3(Koutmax, nnodes), 256, 0, st>>>(A.nodes, A, U, ldq);
+    }
+    if (Tmax > 0) {
+      GEV_COUNT(s);
+      k_gather<<<dim3(Tmax, nnodes), 256, 0, st>>>(A.nodes, A, Qa, ldq, Qg, Qb);
+    }
     GEV_TRY(last_error());
     // eigenvector update: top rows use the top-only and mixed columns, bottom rows the mixed and
     // bottom-only ones
@@ -651,12 +672,15 @@ int stedc(Sys& s, const double* d, const double* e, int k, double* w, double* Z,
       else
         GEV_CUDA_TRY(cudaMemset2DAsync(Qb + x.m + (long long)x.a * ldq, ldq * 8, 0, n2 * 8, x.Kout, st));
     }
+    GEV_COUNT(s);
     k_finalize<<<dim3(cdiv(Tmax, 256), nnodes), 256, 0, st>>>(A.nodes, A, w);
     GEV_TRY(last_error());
+    GEV_COUNT(s);
     k_copy_int<<<eb, 256, 0, st>>>(n, A.colmap2, A.colmap);
     std::swap(Qa, Qb);
   }
   // the k lowest eigenvectors
+  GEV_COUNT(s);
   k_output<<<k, 256, 0, st>>>(n, k, Qa, ldq, A.colmap, Z, ldz);
   GEV_TRY(last_error());
   GEV_CUDA_TRY(cudaMemsetAsync(&s.status[ST_DEFLATED], 0, sizeof(int), st));

@@ -9,6 +9,8 @@
 // Triangular operands are handled per element at load time (the zero triangle is never read) and
 // per tile (k ranges and output tiles that are identically zero are skipped), which is what makes
 // TRMM / SYRK / the Multiply step cost their algorithmic flops.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace gev {
@@ -200,10 +202,56 @@ __global__ void splitk_reduce(GemmP<T> p) {
   }
 }
 
+// sum over j = 0..J of max(0, min(ah, bh(j)) - max(al, bl(j))): the multiply-adds of one output row
+// (bl/bh: the k range allowed by the zero pattern of op(B) in column j).
+long double row_fmas(long long al, long long ah, int tri_b, long long J) {
+  if (J < 0 || ah <= al) return 0.0L;
+  long double s = 0.0L;
+  if (tri_b == 0) return (long double)(ah - al) * (long double)(J + 1);
+  if (tri_b == 1) {  // op(B)[k,j] = 0 for k < j
+    const long long j1 = std::min(J, al);
+    if (j1 >= 0) s += (long double)(ah - al) * (long double)(j1 + 1);
+    const long long lo = std::max(al + 1, 0LL), hi = std::min(J, ah - 1);
+    if (hi >= lo) s += (long double)(hi - lo + 1) * ah - (long double)(lo + hi) * (hi - lo + 1) / 2.0L;
+    return s;
+  }
+  // tri_b == 2: op(B)[k,j] = 0 for k > j
+  const long long lo = std::max(al, 0LL), hi = std::min(J, ah - 1);
+  if (hi >= lo) s += (long double)(lo + hi) * (hi - lo + 1) / 2.0L + (long double)(1 - al) * (hi - lo + 1);
+  const long long lo2 = std::max(ah, 0LL);
+  if (J >= lo2) s += (long double)(ah - al) * (long double)(J - lo2 + 1);
+  return s;
+}
+
+template <class T> double algorithmic_flops(const GemmP<T>& p) {
+  long double fma = 0.0L;
+  for (long long i = 0; i < p.M; ++i) {
+    long long al = (p.tri_a == 2) ? i : 0;
+    long long ah = (p.tri_a == 1) ? std::min<long long>(p.K, i + 1) : p.K;
+    const long long J = p.c_lower ? std::min<long long>(p.N - 1, i) : p.N - 1;
+    fma += row_fmas(al, ah, p.tri_b, J);
+  }
+  return (double)(fma * (is_cx<T>::value ? 8.0L : 2.0L));
+}
+
 }  // namespace
 
 template <class T> void gemm(Sys& s, GemmP<T> p) {
   if (p.M <= 0 || p.N <= 0) return;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  if (s.account) {
+    const size_t need = 2 * (size_t)(s.gemm_used + 1);
+    while (s.gemm_ev.size() < need) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      s.gemm_ev.push_back(e);
+    }
+    ev0 = s.gemm_ev[2 * s.gemm_used];
+    ev1 = s.gemm_ev[2 * s.gemm_used + 1];
+    if ((int)s.gemm_fl.size() <= s.gemm_used) s.gemm_fl.resize(s.gemm_used + 1);
+    s.gemm_fl[s.gemm_used] = algorithmic_flops(p);
+    cudaEventRecord(ev0, s.stream);
+  }
   dim3 grid(cdiv(p.M, BM), cdiv(p.N, BN), 1);
   long long tiles = (long long)grid.x * grid.y;
   if (p.c_lower) tiles = (tiles + grid.x) / 2;
@@ -226,13 +274,33 @@ template <class T> void gemm(Sys& s, GemmP<T> p) {
       grid.z = ks;
     }
   }
+  GEV_COUNT(s);
   gemm_kernel<T><<<grid, NT, 0, s.stream>>>(p);
   if (p.ksplit > 1) {
     long long total = (long long)p.M * p.N;
     unsigned blocks = cdiv(total, 256);
     if (blocks > 8u * s.sms) blocks = 8u * s.sms;
+    GEV_COUNT(s);
     splitk_reduce<T><<<blocks, 256, 0, s.stream>>>(p);
   }
+  if (s.account) {
+    cudaEventRecord(ev1, s.stream);
+    ++s.gemm_used;
+  }
+}
+
+// Sum the timed GEMM launches of the current call (stream must be synchronised).
+void gemm_account(Sys& s, int* calls, double* ms, double* flops) {
+  double tm = 0.0, fl = 0.0;
+  for (int i = 0; i < s.gemm_used; ++i) {
+    float t = 0.f;
+    cudaEventElapsedTime(&t, s.gemm_ev[2 * i], s.gemm_ev[2 * i + 1]);
+    tm += t;
+    fl += s.gemm_fl[i];
+  }
+  *calls = s.gemm_used;
+  *ms = tm;
+  *flops = fl;
 }
 
 template void gemm<double>(Sys&, GemmP<double>);

@@ -358,6 +358,9 @@ template <class T> int solve_t(Sys& s, const T* H, int ldh, const T* S, int lds,
   };
   T* A = (T*)s.A;
   T* X = (T*)s.X;
+  s.launches = 0;
+  s.gemm_used = 0;
+  s.account = s.opts.timing == 2;
   GEV_CUDA_TRY(cudaMemsetAsync(s.status, 0, sizeof(int) * ST_COUNT, s.stream));
   mark(GEV_STEP_CHOLESKY);
   const bool reuse = (S == nullptr);
@@ -406,6 +409,8 @@ template <class T> int solve_t(Sys& s, const T* H, int ldh, const T* S, int lds,
   if (!s.reuse) s.have_factor = false;
   if (rep) {
     rep->deflated = s.status_h[ST_DEFLATED];
+    rep->launches = s.launches;
+    if (s.account) gemm_account(s, &rep->gemm_calls, &rep->gemm_ms, &rep->gemm_flops);
     if (timing) {
       for (int i = 0; i < GEV_NSTEPS; ++i) {
         float ms = 0.f;

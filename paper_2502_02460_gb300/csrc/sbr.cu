@@ -190,8 +190,7 @@ template <class T> int he2hb(Sys& s, T* A, int lda, int b) {
   const int n = s.n;
   static bool attr = false;
   if (!attr) {
-    GEV_CUDA_TRY(cudaFuncSetAttribute(k_panel_qr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      227 * 1024));
+    GEV_TRY(allow_max_dyn_smem(k_panel_qr<T>));
     attr = true;
   }
   T* V1 = (T*)s.V1;
@@ -230,6 +229,7 @@ template <class T> int he2hb(Sys& s, T* A, int lda, int b) {
     int mm = m, bb = b;
     long long ldp = lda, ldy = n;
     void* args[] = {&mm, &bb, &Pp, &ldp, &Yp, &ldy, &Tp, &nrm_part, &w_part, &alpha_g, &gb, &R, &use_smem};
+    GEV_COUNT(s);
     GEV_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_panel_qr<T>, dim3(G), dim3(NT), args, smem, s.stream));
     // ---- two-sided update of the trailing block
     T* A22 = A + r0 + (long long)r0 * lda;
@@ -257,6 +257,7 @@ template <class T> int he2hb(Sys& s, T* A, int lda, int b) {
     long long total = (long long)n * ldb;
     unsigned blocks = cdiv(total, 256);
     if (blocks > 16u * s.sms) blocks = 16u * s.sms;
+    GEV_COUNT(s);
     k_extract_band<T><<<blocks, 256, 0, s.stream>>>(n, b, A, lda, (T*)s.band, ldb);
     GEV_TRY(last_error());
   }

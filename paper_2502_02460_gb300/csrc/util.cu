@@ -138,30 +138,35 @@ __global__ void k_normalize_phase(int n, T* C, long long ldc) {
 template <class T> int copy_lower(Sys& s, int n, const T* S, int lds, T* A, int lda) {
   if (n <= 0) return 0;
   dim3 g(cdiv(n, TD), cdiv(n, TD)), b(TD, 8);
+  GEV_COUNT(s);
   k_copy_lower<T><<<g, b, 0, s.stream>>>(n, S, lds, A, lda, 0);
   return last_error();
 }
 template <class T> int tril_halfdiag(Sys& s, int n, const T* H, int ldh, T* B, int ldb) {
   if (n <= 0) return 0;
   dim3 g(cdiv(n, TD), cdiv(n, TD)), b(TD, 8);
+  GEV_COUNT(s);
   k_copy_lower<T><<<g, b, 0, s.stream>>>(n, H, ldh, B, ldb, 1);
   return last_error();
 }
 template <class T> int herm_sum(Sys& s, int n, const T* M, int ldm, T* A, int lda) {
   if (n <= 0) return 0;
   dim3 g(cdiv(n, TD), cdiv(n, TD)), b(TD, 8);
+  GEV_COUNT(s);
   k_herm_sum<T><<<g, b, 0, s.stream>>>(n, M, ldm, A, lda);
   return last_error();
 }
 template <class T> int mirror_lower(Sys& s, int n, T* A, int lda) {
   if (n <= 0) return 0;
   dim3 g(cdiv(n, TD), cdiv(n, TD)), b(TD, 8);
+  GEV_COUNT(s);
   k_mirror<T><<<g, b, 0, s.stream>>>(n, A, lda);
   return last_error();
 }
 template <class T> int zero_upper(Sys& s, int n, T* A, int lda) {
   if (n <= 1) return 0;
   dim3 g(cdiv(n, TD), cdiv(n, TD)), b(TD, 8);
+  GEV_COUNT(s);
   k_zero_upper<T><<<g, b, 0, s.stream>>>(n, A, lda);
   return last_error();
 }
@@ -170,11 +175,13 @@ template <class T> int copy2d(Sys& s, int m, int n, const T* src, long long lds,
   long long total = (long long)m * n;
   unsigned blocks = cdiv(total, 256);
   if (blocks > 16u * s.sms) blocks = 16u * s.sms;
+  GEV_COUNT(s);
   k_copy2d<T><<<blocks, 256, 0, s.stream>>>(m, n, src, lds, dst, ldd);
   return last_error();
 }
 template <class T> int normalize_phase(Sys& s, int n, int k, T* C, int ldc) {
   if (n <= 0 || k <= 0) return 0;
+  GEV_COUNT(s);
   k_normalize_phase<T><<<k, 256, 0, s.stream>>>(n, C, ldc);
   return last_error();
 }

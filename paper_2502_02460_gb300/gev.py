@@ -53,12 +53,16 @@ class Opts(ctypes.Structure):
 class Report(ctypes.Structure):
     _fields_ = [("info", ctypes.c_int), ("deflated", ctypes.c_int), ("refine_iters", ctypes.c_int),
                 ("reused_factor", ctypes.c_int), ("refine_resid", ctypes.c_double),
-                ("ms", ctypes.c_double * NSTEPS), ("workspace_bytes", ctypes.c_size_t)]
+                ("ms", ctypes.c_double * NSTEPS), ("workspace_bytes", ctypes.c_size_t),
+                ("launches", ctypes.c_longlong), ("gemm_calls", ctypes.c_int),
+                ("gemm_ms", ctypes.c_double), ("gemm_flops", ctypes.c_double)]
 
     def as_dict(self):
         return {"info": self.info, "deflated": self.deflated, "refine_iters": self.refine_iters,
                 "reused_factor": self.reused_factor, "refine_resid": self.refine_resid,
-                "ms": dict(zip(STEP_NAMES, list(self.ms))), "workspace_bytes": self.workspace_bytes}
+                "ms": dict(zip(STEP_NAMES, list(self.ms))), "workspace_bytes": self.workspace_bytes,
+                "launches": self.launches, "gemm_calls": self.gemm_calls, "gemm_ms": self.gemm_ms,
+                "gemm_flops": self.gemm_flops}
 
 
 _lib = None
@@ -135,7 +139,7 @@ class Solver:
     """One handle (``gev_setup``) for problems of order n: workspace, resident factor, stream."""
 
     def __init__(self, n: int, complex_: bool = False, device=None, mixed: bool = False,
-                 band_b: int = 0, panel_nb: int = 0, timing: bool = False, stream=None,
+                 band_b: int = 0, panel_nb: int = 0, timing: int = 0, stream=None,
                  workspace_limit: int = 0, refine_tol: float = 0.0, refine_max_iter: int = 0):
         import torch
 
@@ -155,7 +159,7 @@ class Solver:
         o.prec = GEV_MIXED if mixed else GEV_PLAIN
         o.band_b = band_b
         o.panel_nb = panel_nb
-        o.timing = 1 if timing else 0
+        o.timing = int(timing)
         o.workspace_limit = workspace_limit
         o.refine_tol = refine_tol
         o.refine_max_iter = refine_max_iter

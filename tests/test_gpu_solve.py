@@ -246,3 +246,24 @@ def test_not_spd_overlap_reports_pivot(dev):
         p = inputs.make_problem(n, 10, seed=3)
         w, _ = s.solve_cm(gv().cm_from_numpy(p.H, dev), gv().cm_from_numpy(p.S, dev), 10)
         assert np.max(np.abs(w.cpu().numpy() - p.lam[:10])) <= 1e-11 * norm1(p.H)
+
+
+@pytest.mark.parametrize("cx", [False, True])
+def test_repeated_solves_are_bitwise_identical(dev, cx):
+    """A handle keeps no state that changes results: repeated solves, and a fresh handle, agree
+    bit for bit (the divide and conquer relies on zero rows outside each eigenvector block)."""
+    n, k = 700, 200
+    p = inputs.make_problem(n, k, seed=31, complex_=cx)
+    Hb, Sb = gv().cm_from_numpy(p.H, dev), gv().cm_from_numpy(p.S, dev)
+    outs = []
+    with gv().Solver(n, complex_=cx, device=dev) as s:
+        for _ in range(3):
+            w, Cb = s.solve_cm(Hb, Sb, k)
+            outs.append((w.cpu().numpy(), gv().numpy_from_cm(Cb)))
+    with gv().Solver(n, complex_=cx, device=dev) as s:
+        w, Cb = s.solve_cm(Hb, Sb, k)
+        outs.append((w.cpu().numpy(), gv().numpy_from_cm(Cb)))
+    for w, C in outs[1:]:
+        assert np.array_equal(w, outs[0][0])
+        assert np.array_equal(C, outs[0][1])
+    assert np.max(np.abs(outs[0][0] - p.lam[:k])) <= 1e-11 * norm1(p.H)
