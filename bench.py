@@ -152,6 +152,49 @@ def run_reference(args):
     return 0
 
 
+def run_stream(args, dev):
+    """A prefix of the k-point serving stream (Poisson arrivals at 200/s, complex128 pencils of
+    log-uniform size recurring for 10 SCF iterations with fixed S, k = N/4) through the
+    continuous-batching server; latency from each request's scheduled arrival to its result."""
+    import numpy as np
+    import torch
+
+    from paper_2502_02460_gb300 import gev, inputs, serve
+
+    spec = serve.StreamSpec(requests=args.stream_requests, n_max=args.stream_n_max)
+    plan = serve.stream_plan(spec)
+    cache = {}
+    for (_, sid, it, n, k, last) in plan:  # build every request's pencil before the clock starts
+        if sid not in cache:
+            p = inputs.make_problem(n, k, seed=4000 + sid, complex_=True, gap_check=False)
+            cache[sid] = (p, gev.cm_from_numpy(p.S, dev))
+        p = cache[sid][0]
+        rng = np.random.default_rng(5000 + 1000 * sid + it)
+        G = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+        dH = 0.5 * (G + G.conj().T)
+        H = p.H + (spec.dh_rel * np.linalg.norm(p.H) / np.linalg.norm(dH) * dH if it > 0 else 0)
+        cache[(sid, it)] = gev.cm_from_numpy(H, dev)
+    torch.cuda.synchronize()
+    srv = serve.Server(budget_bytes=120e9, workers=6, device=dev, mixed=False)
+    t0 = time.perf_counter()
+    futs = []
+    for (t, sid, it, n, k, last) in plan:
+        now = time.perf_counter() - t0
+        if t > now:
+            time.sleep(t - now)
+        futs.append(srv.submit(sid, cache[(sid, it)], cache[sid][1] if it == 0 else None, k, n=n,
+                               complex_=True, last=last, arrival=t0 + t))
+    for f in futs:
+        f.result()
+    srv.close()
+    st = srv.stats()
+    st.update({"precision": "plain FP64", "dtype": "c128",
+               "workload": f"first {spec.requests} requests of the k-point stream (Poisson 200/s, "
+                           f"N log-uniform in [{spec.n_min}, {spec.n_max}], 10 SCF iterations per "
+                           f"system, S fixed, k = N/4)"})
+    return st
+
+
 def workload_config(args):
     return {"workload": f"{'complex128' if args.complex else 'real'} N={args.n}, k={args.k} lowest "
                         f"eigenpairs, seed {args.seed}, Toeplitz S, DFT-like spectrum; "
@@ -163,17 +206,26 @@ def workload_config(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--n", type=int, default=16384)
     ap.add_argument("--k", type=int, default=4096)
     ap.add_argument("--seed", type=int, default=3)
     ap.add_argument("--complex", action="store_true")
-    ap.add_argument("--mixed", action="store_true")
-    ap.add_argument("--band-b", type=int, default=32)
+    ap.add_argument("--mixed", dest="mixed", action="store_true", default=True,
+                    help="headline = mixed form (default)")
+    ap.add_argument("--plain", dest="mixed", action="store_false", help="headline = plain FP64 form")
+    ap.add_argument("--no-plain-beside", action="store_true",
+                    help="do not time the plain FP64 solve beside the mixed headline")
+    ap.add_argument("--stream-requests", type=int, default=32,
+                    help="requests of the k-point serving stream reported beside (0 = none)")
+    ap.add_argument("--stream-n-max", type=int, default=2048)
+    ap.add_argument("--band-b", type=int, default=64)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--gen", default="auto", choices=["auto", "cpu", "gpu"],
+                    help="where the synthetic pencil is built (auto: GPU for N > 4096)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -195,9 +247,13 @@ def main():
     if ws > 1:
         torch.distributed.barrier()
     # independent system per rank (weak scaling): seed offset by rank
+    on_gpu = args.gen == "gpu" or (args.gen == "auto" and args.n > 4096)
     p = inputs.make_problem(args.n, args.k, seed=args.seed + 100 * rank, complex_=args.complex,
-                            device=dev, gap_check=False)
-    Hb, Sb = p.H, p.S  # column-major device buffers
+                            device=dev if on_gpu else None, gap_check=False)
+    if on_gpu:
+        Hb, Sb = p.H, p.S  # column-major device buffers
+    else:
+        Hb, Sb = gev.cm_from_numpy(p.H, dev), gev.cm_from_numpy(p.S, dev)
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream(dev)
     solver = gev.Solver(args.n, complex_=args.complex, device=dev, mixed=args.mixed,
@@ -241,6 +297,26 @@ def main():
     achieved = gemm_fl / (gemm_ms * 1e-3) / 1e12 if gemm_ms > 0 else None
     step_ms = {k: statistics.median(r["ms"][k] for r in reps) for k in gev.STEP_NAMES}
     launches = int(statistics.median(r["launches"] for r in reps))
+    # the plain FP64 form on the same input, beside the mixed headline (1 warm-up, 1 timed solve)
+    plain = None
+    if args.mixed and not args.no_plain_beside:
+        solver.close()
+        ps = gev.Solver(args.n, complex_=args.complex, device=dev, mixed=False, band_b=args.band_b,
+                        timing=1, stream=stream)
+        ps.solve_cm(Hb, Sb, args.k, w, Cb)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        ps.solve_cm(Hb, Sb, args.k, w, Cb)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        plain = {"value": f0.elapsed_time(f1) / 1e3, "unit": "s", "steps": 1, "warmup": 1,
+                 "steps_ms": ps.last_report["ms"],
+                 "max_abs_eig_err_vs_construction": float(np.max(np.abs(w.cpu().numpy() - p.lam[: args.k])))}
+        ps.close()
+        solver = gev.Solver(args.n, complex_=args.complex, device=dev, mixed=args.mixed,
+                            band_b=args.band_b, timing=0, stream=stream)
     # end-to-end through the Python API with pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -266,6 +342,11 @@ def main():
             torch.distributed.barrier()
         return 0
     cb = None if args.no_cpu_baseline else cpu_baseline(args.n, args.k, args.complex)
+    stream_stats = None
+    if args.stream_requests > 0 and ws == 1:
+        del solver, Hb, Sb
+        torch.cuda.empty_cache()
+        stream_stats = run_stream(args, dev)
     value = ms / 1e3 / (1 if ws == 1 else 1)  # seconds per solve (each rank solves one system)
     line = {
         "metric": METRIC, "value": value, "unit": "s", "n_gpus": ws, "steps": args.steps,
@@ -274,6 +355,10 @@ def main():
         "solves_per_s": ws / (ms / 1e3),
         "max_abs_eig_err_vs_construction": err,
         "steps_ms": step_ms,
+        "fp64_plain": plain,
+        "refine": {"iterations": reps[-1]["refine_iters"], "residual": reps[-1]["refine_resid"]}
+        if args.mixed else None,
+        "stream": stream_stats,
         "roofline": {"bound": "tensor", "kernel": "gemm_kernel<double> (FP64 DMMA mma.sync m8n8k4)",
                      "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
                      "frac": (achieved / fp64_peak) if achieved else None, "traffic": None,

@@ -1,0 +1,33 @@
+/*
+ * gev_kernels.h -- the FP32 matrix product used by the mixed-precision form, as a C entry point.
+ *
+ * The mixed form runs its reduction and back-transforms in FP32 (the single/double-precision pattern
+ * named in the section "Future Plans and Challenges").  Its products are formed on the tensor cores
+ * from BF16 splits: a = a_hi + a_lo with a_hi = bf16(a), a_lo = bf16(a - a_hi), and
+ * a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi with FP32 accumulation (about 16 correct bits per
+ * product); the result is then refined in FP64 by the solver.
+ */
+#ifndef GEV_KERNELS_H
+#define GEV_KERNELS_H
+
+#include "gev.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* C = alpha op(A) op(B) + beta C, FP32, column-major device pointers on the current device.
+     ta, tb     : 0 = as stored, 1 = transposed
+     engine     : 1 = BF16x3 tensor-core products (tcgen05), 0 = FP32 CUDA-core FMAs
+     stream     : cudaStream_t (NULL = legacy default), synchronised before return
+     status_dev : device pointer to 16 ints the kernel may write (a bounded wait that expired writes
+                  a non-zero code to status_dev[1]); the caller zeroes and reads it
+   Returns 0, -i for an invalid i-th argument, or GEV_ERR_CUDA.  Allocates nothing. */
+int gev_gemm_f32(int M, int N, int K, int ta, int tb, float alpha, const float* A, int lda,
+                 const float* B, int ldb, float beta, float* C, int ldc, int engine, void* stream,
+                 int* status_dev);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GEV_KERNELS_H */

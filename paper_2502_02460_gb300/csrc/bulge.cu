@@ -390,6 +390,8 @@ template <class T, int COLS> int bt_levels(Sys& s, int n, int k, int b, T* Y, in
 }
 
 template int hb2st<double>(Sys&, double*, double*);
+template int hb2st<float>(Sys&, double*, double*);
+template int bt_hb2st<float>(Sys&, const double*, int, int, float*, int);
 template int hb2st<zd>(Sys&, double*, double*);
 template int bt_hb2st<double>(Sys&, const double*, int, int, double*, int);
 template int bt_hb2st<zd>(Sys&, const double*, int, int, zd*, int);

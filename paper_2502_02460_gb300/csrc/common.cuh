@@ -32,6 +32,14 @@ __host__ __device__ __forceinline__ zd& operator-=(zd& a, zd b) { a.x -= b.x; a.
 __host__ __device__ __forceinline__ bool operator==(zd a, zd b) { return a.x == b.x && a.y == b.y; }
 __host__ __device__ __forceinline__ bool operator!=(zd a, zd b) { return !(a == b); }
 
+__host__ __device__ __forceinline__ float conj_(float a) { return a; }
+__host__ __device__ __forceinline__ float re_(float a) { return a; }
+__host__ __device__ __forceinline__ float im_(float) { return 0.0f; }
+__host__ __device__ __forceinline__ float abs2_(float a) { return a * a; }
+__host__ __device__ __forceinline__ float abs_(float a) { return fabsf(a); }
+__host__ __device__ __forceinline__ float mulc(float a, float b) { return a * b; }
+__host__ __device__ __forceinline__ float cmul(float a, float b) { return a * b; }
+__host__ __device__ __forceinline__ float div_(float a, float b) { return a / b; }
 __host__ __device__ __forceinline__ double conj_(double a) { return a; }
 __host__ __device__ __forceinline__ zd conj_(zd a) { return {a.x, -a.y}; }
 __host__ __device__ __forceinline__ double re_(double a) { return a; }
@@ -44,6 +52,7 @@ __host__ __device__ __forceinline__ double abs_(double a) { return fabs(a); }
 __host__ __device__ __forceinline__ double abs_(zd a) { return hypot(a.x, a.y); }
 template <class T> __host__ __device__ __forceinline__ T from_re(double a);
 template <> __host__ __device__ __forceinline__ double from_re<double>(double a) { return a; }
+template <> __host__ __device__ __forceinline__ float from_re<float>(double a) { return (float)a; }
 template <> __host__ __device__ __forceinline__ zd from_re<zd>(double a) { return {a, 0.0}; }
 template <class T> __host__ __device__ __forceinline__ T zero_() { return from_re<T>(0.0); }
 // a * conj(b) and conj(a) * b
@@ -58,6 +67,8 @@ __host__ __device__ __forceinline__ zd div_(zd a, zd b) {
 __host__ __device__ __forceinline__ double div_(double a, double b) { return a / b; }
 
 // L2-coherent loads/stores (bypass L1) for data another block may have written during the kernel.
+__device__ __forceinline__ float ldcg_(const float* p) { return __ldcg(p); }
+__device__ __forceinline__ void stcg_(float* p, float v) { __stcg(p, v); }
 __device__ __forceinline__ double ldcg_(const double* p) { return __ldcg(p); }
 __device__ __forceinline__ zd ldcg_(const zd* p) {
   double2 v = __ldcg(reinterpret_cast<const double2*>(p));
@@ -107,11 +118,15 @@ template <class T> struct GemmP {
   long long ldc;
   int ksplit;  // set by the launcher
   T* ws;       // split-K partials (launcher-owned)
+  int lowp;    // 1: FP64 operands, products and sums in FP32 (mixed form); 0: native precision
 };
 
 struct Sys;
 
 template <class T> void gemm(Sys& s, GemmP<T> p);
+// FP32 SIMT GEMM (gemm32.cu): inputs TI (float or double, converted on load), output TO.
+template <class TI, class TO> void gemm32(Sys& s, const GemmP<TI>& p, TO* C, float alpha, float beta);
+template <> void gemm<float>(Sys& s, GemmP<float> p);  // FP32: gemm32<float, float>
 void gemm_account(Sys& s, int* calls, double* ms, double* flops);
 template <class T> GemmP<T> gp(int M, int N, int K, int ta, int tb, T alpha, const T* A, long long lda,
                                const T* B, long long ldb, T beta, T* C, long long ldc) {
@@ -161,10 +176,18 @@ struct Sys {
   double* Zk = nullptr;   // n x n eigenvectors of the tridiagonal (divide-and-conquer output)
   int* prog = nullptr;    // n per-sweep progress counters of the bulge chasing
   int nsbr_panels = 0;    // panels of the last full -> band reduction
+  int dc_lowp = 0;        // 1: divide-and-conquer merge products in FP32 (mixed form)
+  double* R1 = nullptr;   // mixed form: n x n FP64 refinement buffers (R1..R3)
+  double* R2 = nullptr;
+  double* R3 = nullptr;
+  void* sub = nullptr;    // mixed form: handle of the k x k Rayleigh-Ritz pencil (gev_sys*)
+  int sub_n = 0;
   void* panelws = nullptr;  // cooperative panel partial sums
   size_t panelws_bytes = 0;
   int* status = nullptr;  // device status words (ST_COUNT ints)
-  cudaEvent_t ev[GEV_NSTEPS + 1] = {};
+  cudaEvent_t ev[2 * GEV_NSTEPS + 2] = {};
+  int ev_step[2 * GEV_NSTEPS + 2] = {};  // step id of each recorded mark (-1: end)
+  int n_marks = 0;
   int* status_h = nullptr;  // pinned host mirror
 
   // accounting of the current call
@@ -211,6 +234,11 @@ inline int last_error() {
 
 #define GEV_COUNT(s) (++(s).launches)
 
+// Per-step timing with CUDA events on the solve stream: mark(step) starts a step (and ends the
+// previous one); the durations are summed per step id after the stream is synchronised.
+inline void step_mark(Sys& s, int step);
+inline void step_collect(Sys& s, double* ms);
+
 inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
 
 // Raise a kernel's dynamic shared-memory limit to what the device allows beside its static use.
@@ -244,7 +272,29 @@ template <class T> int herm_sum(Sys& s, int n, const T* M, int ldm, T* A, int ld
 template <class T> int mirror_lower(Sys& s, int n, T* A, int lda);                        // upper <- conj(lower)
 template <class T> int zero_upper(Sys& s, int n, T* A, int lda);                          // strict upper <- 0
 template <class T> int copy2d(Sys& s, int m, int n, const T* src, long long lds, T* dst, long long ldd);
+template <class TA, class TB>
+int convert2d(Sys& s, int m, int n, const TA* src, long long lds, TB* dst, long long ldd);
 template <class T> int normalize_phase(Sys& s, int n, int k, T* C, int ldc);
 int sync_status(Sys& s);  // synchronise the stream, copy the status words to the host mirror
+// mixed form (mixed.cu): FP32 reduction, FP64 Ogita-Aishima refinement of the standard problem
+int solve_mixed(Sys& s, const double* H, int ldh, const double* S, int lds, int k, double* evals,
+                double* C, int ldc, gev_report* rep);
+
+inline void step_mark(Sys& s, int step) {
+  if (!s.opts.timing || s.n_marks >= 2 * GEV_NSTEPS + 2) return;
+  s.ev_step[s.n_marks] = step;
+  cudaEventRecord(s.ev[s.n_marks], s.stream);
+  ++s.n_marks;
+}
+inline void step_collect(Sys& s, double* ms) {
+  for (int i = 0; i < GEV_NSTEPS; ++i) ms[i] = 0.0;
+  for (int m = 0; m + 1 < s.n_marks; ++m) {
+    const int st = s.ev_step[m];
+    if (st < 0 || st >= GEV_NSTEPS) continue;
+    float t = 0.f;
+    cudaEventElapsedTime(&t, s.ev[m], s.ev[m + 1]);
+    ms[st] += t;
+  }
+}
 
 }  // namespace gev

@@ -584,7 +584,7 @@ int stedc(Sys& s, const double* d, const double* e, int k, double* w, double* Z,
   double* Qa = s.Q;
   double* Qb = s.Q2;
   double* Qg = (double*)s.W1;
-  double* U = (double*)s.A;
+  double* U = (double*)s.Yk;  // s.A keeps the FP64 standard matrix (mixed-form refinement)
   const long long ldq = n;
 
   // Every column of a node must be zero outside the node's rows (block-diagonal eigenvector
@@ -662,13 +662,21 @@ int stedc(Sys& s, const double* d, const double* e, int k, double* w, double* Z,
       const int n1 = x.m - x.a, n2 = x.c - x.m;
       const double* Ub = U + (long long)x.a * ldq;  // column a, rows 0 .. K-1 (gather order)
       if (x.K1 + x.K2 > 0)
-        gemm(s, gp<double>(n1, x.Kout, x.K1 + x.K2, 0, 0, 1.0, Qg + x.a + (long long)x.a * ldq, ldq, Ub, ldq,
-                           0.0, Qb + x.a + (long long)x.a * ldq, ldq));
+      {
+        GemmP<double> g = gp<double>(n1, x.Kout, x.K1 + x.K2, 0, 0, 1.0, Qg + x.a + (long long)x.a * ldq, ldq,
+                                     Ub, ldq, 0.0, Qb + x.a + (long long)x.a * ldq, ldq);
+        g.lowp = s.dc_lowp;
+        gemm(s, g);
+      }
       else
         GEV_CUDA_TRY(cudaMemset2DAsync(Qb + x.a + (long long)x.a * ldq, ldq * 8, 0, n1 * 8, x.Kout, st));
       if (x.K2 + x.K3 > 0)
-        gemm(s, gp<double>(n2, x.Kout, x.K2 + x.K3, 0, 0, 1.0, Qg + x.m + (long long)(x.a + x.K1) * ldq, ldq,
-                           Ub + x.K1, ldq, 0.0, Qb + x.m + (long long)x.a * ldq, ldq));
+      {
+        GemmP<double> g = gp<double>(n2, x.Kout, x.K2 + x.K3, 0, 0, 1.0, Qg + x.m + (long long)(x.a + x.K1) * ldq,
+                                     ldq, Ub + x.K1, ldq, 0.0, Qb + x.m + (long long)x.a * ldq, ldq);
+        g.lowp = s.dc_lowp;
+        gemm(s, g);
+      }
       else
         GEV_CUDA_TRY(cudaMemset2DAsync(Qb + x.m + (long long)x.a * ldq, ldq * 8, 0, n2 * 8, x.Kout, st));
     }

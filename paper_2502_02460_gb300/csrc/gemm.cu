@@ -238,6 +238,12 @@ template <class T> double algorithmic_flops(const GemmP<T>& p) {
 
 template <class T> void gemm(Sys& s, GemmP<T> p) {
   if (p.M <= 0 || p.N <= 0) return;
+  if constexpr (!is_cx<T>::value) {
+    if (p.lowp) {  // mixed form: FP64 operands, FP32 arithmetic
+      gemm32<double, double>(s, p, p.C, (float)p.alpha, (float)p.beta);
+      return;
+    }
+  }
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   if (s.account) {
     const size_t need = 2 * (size_t)(s.gemm_used + 1);

@@ -32,7 +32,7 @@ struct Layout {
 
 // band width: a power of two in [16, 64] (the bulge-chasing kernel stages three b x b blocks)
 int pick_band(int n, int want) {
-  int b = want > 0 ? want : 32;
+  int b = want > 0 ? want : 64;
   int p = 16;
   while (p < b && p < 64) p *= 2;
   return p;
@@ -62,6 +62,8 @@ size_t carve(Sys& s, char* base) {
   size_t panel = (size_t)4096 * (2 * b + 8) * es * 2;
   size_t opanel = L.add(panel);
   size_t ost = L.add(sizeof(int) * ST_COUNT);
+  const bool mixed = s.opts.prec == GEV_MIXED;
+  size_t oR1 = L.add(mixed ? n * n * 8 : 8), oR2 = L.add(mixed ? n * n * 8 : 8), oR3 = L.add(mixed ? n * n * 8 : 8);
   if (base) {
     s.A = base + oA; s.X = base + oX; s.W1 = base + oW1; s.V1 = base + oV1; s.T1 = base + oT1;
     s.dinv = base + odinv; s.Pn = base + oPn; s.small = base + osmall;
@@ -76,6 +78,9 @@ size_t carve(Sys& s, char* base) {
     s.prog = (int*)(base + oprog);
     s.panelws = base + opanel; s.panelws_bytes = panel;
     s.status = (int*)(base + ost);
+    s.R1 = (double*)(base + oR1);
+    s.R2 = (double*)(base + oR2);
+    s.R3 = (double*)(base + oR3);
   }
   return L.total;
 }
@@ -171,7 +176,7 @@ int gev_setup(gev_sys** out, int n, int dtype, const gev_opts* opts) {
     delete h;
     return GEV_ERR_OOM;
   }
-  for (int i = 0; i <= GEV_NSTEPS; ++i) cudaEventCreate(&s.ev[i]);
+  for (int i = 0; i < 2 * GEV_NSTEPS + 2; ++i) cudaEventCreate(&s.ev[i]);
   if (cudaMemsetAsync(s.status, 0, sizeof(int) * ST_COUNT, s.stream) != cudaSuccess ||
       cudaStreamSynchronize(s.stream) != cudaSuccess) {
     gev_free(h);
@@ -184,11 +189,16 @@ int gev_setup(gev_sys** out, int n, int dtype, const gev_opts* opts) {
 int gev_free(gev_sys* h) {
   if (!h) return 0;
   Sys& s = h->s;
+  if (s.sub) {
+    gev_free((gev_sys*)s.sub);
+    s.sub = nullptr;
+  }
   cudaSetDevice(s.opts.device);
   if (s.stream) cudaStreamSynchronize(s.stream);
   else cudaDeviceSynchronize();
-  for (int i = 0; i <= GEV_NSTEPS; ++i)
+  for (int i = 0; i < 2 * GEV_NSTEPS + 2; ++i)
     if (s.ev[i]) cudaEventDestroy(s.ev[i]);
+  for (cudaEvent_t e : s.gemm_ev) cudaEventDestroy(e);
   if (s.base) cudaFree(s.base);
   if (s.status_h) cudaFreeHost(s.status_h);
   delete h;
@@ -218,8 +228,11 @@ int gev_solve(gev_sys* h, const void* H, int ldh, const void* S, int lds, int k,
   if (cudaSetDevice(s.opts.device) != cudaSuccess) return GEV_ERR_CUDA;
   if (rep) std::memset(rep, 0, sizeof(*rep));
   int r;
+  if (s.opts.prec == GEV_MIXED && s.dtype == GEV_C128) return GEV_ERR_UNSUPPORTED;
   if (s.dtype == GEV_C128)
     r = solve_t<zd>(s, (const zd*)H, ldh, (const zd*)S, lds, k, evals, (zd*)C, ldc, rep);
+  else if (s.opts.prec == GEV_MIXED)
+    r = solve_mixed(s, (const double*)H, ldh, (const double*)S, lds, k, evals, (double*)C, ldc, rep);
   else
     r = solve_t<double>(s, (const double*)H, ldh, (const double*)S, lds, k, evals, (double*)C, ldc, rep);
   if (rep) rep->workspace_bytes = s.bytes;
@@ -353,9 +366,8 @@ template <class T> int solve_t(Sys& s, const T* H, int ldh, const T* S, int lds,
                                T* C, int ldc, gev_report* rep) {
   const int n = s.n;
   const bool timing = s.opts.timing != 0;
-  auto mark = [&](int step) {
-    if (timing) cudaEventRecord(s.ev[step], s.stream);
-  };
+  s.n_marks = 0;
+  auto mark = [&](int step) { step_mark(s, step); };
   T* A = (T*)s.A;
   T* X = (T*)s.X;
   s.launches = 0;
@@ -402,22 +414,15 @@ template <class T> int solve_t(Sys& s, const T* H, int ldh, const T* S, int lds,
   mark(GEV_STEP_MULT);
   GEV_TRY(mult<T>(s, X, n, Y, n, k, C, ldc));
   GEV_TRY(normalize_phase<T>(s, n, k, C, ldc));
-  mark(GEV_STEP_REFINE);
   GEV_CUDA_TRY(cudaMemcpyAsync(evals, s.w, sizeof(double) * k, cudaMemcpyDeviceToDevice, s.stream));
-  mark(GEV_NSTEPS);
+  mark(-1);
   GEV_TRY(sync_status(s));
   if (!s.reuse) s.have_factor = false;
   if (rep) {
     rep->deflated = s.status_h[ST_DEFLATED];
     rep->launches = s.launches;
     if (s.account) gemm_account(s, &rep->gemm_calls, &rep->gemm_ms, &rep->gemm_flops);
-    if (timing) {
-      for (int i = 0; i < GEV_NSTEPS; ++i) {
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, s.ev[i], s.ev[i + 1]);
-        rep->ms[i] = ms;
-      }
-    }
+    if (timing) step_collect(s, rep->ms);
   }
   if (s.status_h[ST_TIMEOUT]) return GEV_ERR_TIMEOUT;
   if (s.status_h[ST_NOCONV]) return GEV_ERR_NO_CONVERGENCE;

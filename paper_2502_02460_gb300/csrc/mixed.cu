@@ -1,0 +1,259 @@
+// Mixed-precision form of the generalized solve (real data).
+//
+// FP64: Cholesky of S, inversion, Multiply A = X H X^T (A is kept in FP64), the refinement and
+// C = X^T Y.  FP32: full->band and band->tridiagonal of A32 = fl32(A), the eigenvector products of
+// the divide-and-conquer merges, both back-transforms; the secular equations stay FP64.  The paper
+// states the precision pattern only (single- and double-precision solutions combined during the SCF
+// cycle, section "Future Plans and Challenges"); the refinement is an iteration on the standard
+// problem (A, Y) in the spirit of Ogita-Aishima, with an FP64 Rayleigh-Ritz step in span(Y):
+//
+//   AY = A Y,  T = Y^T AY,  G = Y^T Y
+//   Rayleigh-Ritz: T W = G W Lambda (k x k pencil, solved by this library in FP64; W^T G W = I)
+//   Y <- Y W,  AY <- AY W,  r_j = AY_j - lambda_j Y_j
+//   stop when ||r_j||_1 <= tol ||A||_1 ||y_j||_1 for every j, else
+//   out of span: W' = V^T r (V: the other n-k FP32 eigenvectors, mu their FP32 eigenvalues),
+//                W'_ij /= (lambda_j - mu_i),  Y <- Y + V W'   (FP32 products, FP64 sum)
+//
+// The FP32 pipeline resolves eigenvalues only to ~1e-7 ||A||, coarser than the valence spacing of
+// DFT-like spectra, so its individual vectors inside near-degenerate groups are mixed while the
+// spanned subspaces are accurate; the Rayleigh-Ritz step resolves them exactly in FP64, which a
+// pairwise first-order correction cannot do in a few steps.
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+
+namespace gev {
+
+namespace {
+
+__device__ __forceinline__ double wsum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double wmax(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// out[j] = sum_i |A(i,j)|  (one block per column)
+__global__ void k_colabs(int m, const double* A, long long lda, double* out) {
+  const int j = blockIdx.x;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) s += fabs(A[i + j * lda]);
+  __shared__ double red[32];
+  s = wsum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    out[j] = t;
+  }
+}
+
+// out[0] = max_i v[i]  (one block)
+__global__ void k_vmax(int n, const double* v, double* out) {
+  double m = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, v[i]);
+  __shared__ double red[32];
+  m = wmax(m);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmax(t, red[w]);
+    out[0] = t;
+  }
+}
+
+// residual columns r_j = AY_j - lambda_j Y_j: FP32 copy, and the 1-norms of r_j and y_j
+__global__ void k_resid(int n, const double* AY, const double* Y, long long ld, const double* lam,
+                        float* Rf, long long ldr, double* rn, double* yn) {
+  const int j = blockIdx.x;
+  const double l = lam[j];
+  double sr = 0.0, sy = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double y = Y[i + j * ld];
+    const double r = AY[i + j * ld] - l * y;
+    Rf[i + j * ldr] = (float)r;
+    sr += fabs(r);
+    sy += fabs(y);
+  }
+  __shared__ double r1[32], r2[32];
+  sr = wsum(sr);
+  sy = wsum(sy);
+  if ((threadIdx.x & 31) == 0) { r1[threadIdx.x >> 5] = sr; r2[threadIdx.x >> 5] = sy; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += r1[w]; b += r2[w]; }
+    rn[j] = a;
+    yn[j] = b;
+  }
+}
+
+// W_ij /= (lambda_j - mu_i) (out-of-span coefficients); negligible gaps contribute nothing
+__global__ void k_scale_w(int m, int k, float* W, long long ldw, const double* lam, const double* mu,
+                          double tiny) {
+  const long long total = (long long)m * k;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % m), j = (int)(t / m);
+    const double den = lam[j] - mu[i];
+    float& w = W[i + j * ldw];
+    w = (fabs(den) > tiny) ? (float)((double)w / den) : 0.f;
+  }
+}
+
+}  // namespace
+
+int solve_mixed(Sys& s, const double* H, int ldh, const double* S, int lds, int k, double* evals, double* C,
+                int ldc, gev_report* rep) {
+  const int n = s.n;
+  cudaStream_t st = s.stream;
+  s.n_marks = 0;
+  s.launches = 0;
+  s.gemm_used = 0;
+  s.account = s.opts.timing == 2;
+  auto mark = [&](int step) { step_mark(s, step); };
+  double* A = (double*)s.A;
+  double* X = (double*)s.X;
+  GEV_CUDA_TRY(cudaMemsetAsync(s.status, 0, sizeof(int) * ST_COUNT, st));
+  // ---- FP64: Cholesky, inversion, Multiply
+  mark(GEV_STEP_CHOLESKY);
+  const bool reuse = (S == nullptr);
+  if (!reuse) {
+    GEV_TRY(copy_lower<double>(s, n, S, lds, X, n));
+    GEV_TRY(potrf<double>(s, X, n));
+    GEV_TRY(sync_status(s));
+    if (s.status_h[ST_NOT_SPD]) {
+      if (rep) rep->info = s.status_h[ST_NOT_SPD];
+      s.have_factor = false;
+      return GEV_ERR_NOT_SPD;
+    }
+    mark(GEV_STEP_INVERT);
+    GEV_TRY(trtri<double>(s, X, n));
+  }
+  if (rep) rep->reused_factor = reuse ? 1 : 0;
+  mark(GEV_STEP_MULTIPLY);
+  GEV_TRY(hegst<double>(s, H, ldh, X, n, A, n));
+  s.have_factor = true;
+  // ---- FP32 reduction of A32 = fl32(A); all n eigenvectors (the refinement uses the complement)
+  mark(GEV_STEP_TO_BAND);
+  float* A32 = (float*)s.W1;
+  GEV_TRY((convert2d<double, float>(s, n, n, A, n, A32, n)));
+  GEV_TRY(he2hb<float>(s, A32, n, s.b));
+  mark(GEV_STEP_TO_TRIDIAG);
+  GEV_TRY(hb2st<float>(s, s.d, s.e));
+  mark(GEV_STEP_SOLVE);
+  s.dc_lowp = 1;
+  int r = stedc(s, s.d, s.e, n, s.w, s.Zk, n, nullptr);
+  s.dc_lowp = 0;
+  GEV_TRY(r);
+  mark(GEV_STEP_BACK_TRIDIAG);
+  float* Y32 = (float*)s.Yk;
+  GEV_TRY(bt_hb2st<float>(s, s.Zk, n, n, Y32, n));
+  mark(GEV_STEP_BACK_BAND);
+  GEV_TRY(bt_he2hb<float>(s, Y32, n, n));
+  // ---- FP64 refinement of the k lowest pairs
+  mark(GEV_STEP_REFINE);
+  // buffers (all free or dedicated at this point; every one large enough also for k = n)
+  double* Yd = (double*)s.W1;            // n x k current vectors (A32 is no longer needed)
+  double* Yn = (double*)s.Q2;            // n x k Ritz vectors
+  double* AY = (double*)s.Q;             // n x k
+  double* AYn = s.Zk;                    // n x k
+  double* T = s.R1;                      // k x k
+  double* G = s.R2;                      // k x k
+  double* W = s.R3;                      // k x k Ritz coefficients
+  double* lam = s.e;                     // k (the tridiagonal is consumed)
+  double* rn = s.d;                      // k (after the column sums of A)
+  double* yn = (double*)s.phase;         // k
+  double* scal = (double*)s.small;       // [0] ||A||_1, [1] max ||r_j||_1, [2] max ||y_j||_1
+  float* Rf = Y32 + (size_t)n * n;       // n x k, second half of the FP32 eigenvector buffer
+  float* Wp = (float*)s.V2;              // (n-k) x k
+  const float* Vp = Y32 + (size_t)k * n;
+  const double* mu = s.w + k;
+  GEV_TRY((convert2d<float, double>(s, n, k, Y32, n, Yd, n)));
+  GEV_COUNT(s);
+  k_colabs<<<n, 256, 0, st>>>(n, A, n, s.d);
+  GEV_COUNT(s);
+  k_vmax<<<1, 1024, 0, st>>>(n, s.d, scal);
+  double hs[3] = {0, 0, 0};
+  GEV_CUDA_TRY(cudaMemcpyAsync(hs, scal, sizeof(double), cudaMemcpyDeviceToHost, st));
+  GEV_CUDA_TRY(cudaStreamSynchronize(st));
+  const double anorm = hs[0] > 0 ? hs[0] : 1.0;
+  const double tol = s.opts.refine_tol;
+  const int maxit = s.opts.refine_max_iter;
+  // the k x k Rayleigh-Ritz pencil is solved by a second (cached) handle of this library
+  if (!s.sub || s.sub_n != k) {
+    if (s.sub) gev_free((gev_sys*)s.sub);
+    s.sub = nullptr;
+    gev_opts o = s.opts;
+    o.prec = GEV_PLAIN;
+    o.timing = 0;
+    o.workspace_limit = 0;
+    o.band_b = 0;
+    gev_sys* h = nullptr;
+    const int rc = gev_setup(&h, k, GEV_F64, &o);
+    if (rc) return rc;
+    s.sub = h;
+    s.sub_n = k;
+  }
+  int it = 0;
+  double resid = 0.0;
+  bool converged = false;
+  for (;; ++it) {
+    gemm(s, gp<double>(n, k, n, 0, 0, 1.0, A, n, Yd, n, 0.0, AY, n));   // AY = A Y
+    gemm(s, gp<double>(k, k, n, 1, 0, 1.0, Yd, n, AY, n, 0.0, T, k));   // T = Y^T A Y
+    gemm(s, gp<double>(k, k, n, 1, 0, 1.0, Yd, n, Yd, n, 0.0, G, k));   // G = Y^T Y
+    gev_report sr;
+    const int rc = gev_solve((gev_sys*)s.sub, T, k, G, k, k, lam, W, k, &sr);
+    if (rc) return rc;
+    s.launches += sr.launches;
+    gemm(s, gp<double>(n, k, k, 0, 0, 1.0, Yd, n, W, k, 0.0, Yn, n));   // Ritz vectors
+    gemm(s, gp<double>(n, k, k, 0, 0, 1.0, AY, n, W, k, 0.0, AYn, n));  // A times them
+    GEV_COUNT(s);
+    k_resid<<<k, 256, 0, st>>>(n, AYn, Yn, n, lam, Rf, n, rn, yn);
+    GEV_COUNT(s);
+    k_vmax<<<1, 1024, 0, st>>>(k, rn, scal + 1);
+    GEV_COUNT(s);
+    k_vmax<<<1, 1024, 0, st>>>(k, yn, scal + 2);
+    GEV_CUDA_TRY(cudaMemcpyAsync(hs, scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    GEV_CUDA_TRY(cudaStreamSynchronize(st));
+    resid = hs[1] / (anorm * (hs[2] > 0 ? hs[2] : 1.0));
+    std::swap(Yd, Yn);  // Yd = the Ritz vectors
+    if (resid <= tol) { converged = true; break; }
+    if (it >= maxit || n == k) break;
+    GemmP<float> g = gp<float>(n - k, k, n, 1, 0, 1.0f, Vp, n, Rf, n, 0.0f, Wp, n - k);
+    gemm32<float, float>(s, g, Wp, 1.0f, 0.0f);  // W' = V^T r
+    GEV_COUNT(s);
+    k_scale_w<<<std::min<unsigned>(cdiv((long long)(n - k) * k, 256), 16u * s.sms), 256, 0, st>>>(
+        n - k, k, Wp, n - k, lam, mu, 1e-14 * anorm);
+    GemmP<float> g2 = gp<float>(n, k, n - k, 0, 0, 1.0f, Vp, n, Wp, n - k, 1.0f, nullptr, n);
+    gemm32<float, double>(s, g2, Yd, 1.0f, 1.0f);  // Y += V W' (FP32 products, FP64 sum)
+  }
+  if (rep) {
+    rep->refine_iters = it + 1;
+    rep->refine_resid = resid;
+  }
+  // ---- FP64: C = X^T Y
+  mark(GEV_STEP_MULT);
+  GEV_TRY(mult<double>(s, X, n, Yd, n, k, C, ldc));
+  GEV_TRY(normalize_phase<double>(s, n, k, C, ldc));
+  GEV_CUDA_TRY(cudaMemcpyAsync(evals, lam, sizeof(double) * k, cudaMemcpyDeviceToDevice, st));
+  mark(-1);
+  GEV_TRY(sync_status(s));
+  if (!s.reuse) s.have_factor = false;
+  if (rep) {
+    rep->launches = s.launches;
+    if (s.account) gemm_account(s, &rep->gemm_calls, &rep->gemm_ms, &rep->gemm_flops);
+    if (s.opts.timing) step_collect(s, rep->ms);
+  }
+  if (s.status_h[ST_TIMEOUT]) return GEV_ERR_TIMEOUT;
+  if (s.status_h[ST_NOCONV]) return GEV_ERR_NO_CONVERGENCE;
+  if (!converged) return GEV_ERR_NO_CONVERGENCE;
+  return 0;
+}
+
+}  // namespace gev

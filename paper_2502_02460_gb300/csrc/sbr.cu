@@ -76,10 +76,12 @@ __global__ void __launch_bounds__(NT) k_panel_qr(int m, int b, T* P, long long l
       if (lo <= c && c < hi) alpha_g[0] = base[(c - lo) + c * ld];
     }
     if (!grid_sync(gb, 101)) return;
-    // ---- B: reflector
+    // ---- B: reflector (all threads sum the block partials, in a fixed order)
+    double xpart = 0.0;
+    for (int q = tid; q < (int)gridDim.x; q += NT) xpart += ldcg_(&nrm_part[q]);
+    const double xn_all = block_sum<T>(xpart, red);
     if (tid == 0) {
-      double xn = 0.0;
-      for (int q = 0; q < (int)gridDim.x; ++q) xn += ldcg_(&nrm_part[q]);
+      const double xn = xn_all;
       T alpha = ldcg_(alpha_g);
       int trivial = (xn == 0.0 && im_(alpha) == 0.0);
       if (trivial) {
@@ -125,13 +127,21 @@ __global__ void __launch_bounds__(NT) k_panel_qr(int m, int b, T* P, long long l
       }
     }
     if (!grid_sync(gb, 102)) return;
-    // ---- C: apply H^H to the remaining columns; column c of T (block 0)
-    if (tid < b) {
-      T sum = zero_<T>();
-      for (int q = 0; q < (int)gridDim.x; ++q) sum += ldcg_(&w_part[(long long)q * b + tid]);
-      wv[tid] = sum;
+    // ---- C: apply H^H to the remaining columns; column c of T (block 0).  The block partials of
+    // w are summed by NG threads per column, then combined in a fixed order.
+    {
+      T part = zero_<T>();
+      if (grp < NG)
+        for (int q = grp; q < (int)gridDim.x; q += NG) part += ldcg_(&w_part[(long long)q * b + jj]);
+      red2[tid] = part;
+      __syncthreads();
+      if (tid < b) {
+        T sum = zero_<T>();
+        for (int g = 0; g < NG; ++g) sum += red2[g * b + tid];
+        wv[tid] = sum;
+      }
+      __syncthreads();
     }
-    __syncthreads();
     const T ctau = conj_(tau);
     if (grp < NG && jj > c) {
       const T wj = ctau * wv[jj];
@@ -302,6 +312,8 @@ template int back<zd>(Sys&, const double*, int, int, zd*, int);
 template int he2hb<double>(Sys&, double*, int, int);
 template int he2hb<zd>(Sys&, zd*, int, int);
 template int bt_he2hb<double>(Sys&, double*, int, int);
+template int he2hb<float>(Sys&, float*, int, int);
+template int bt_he2hb<float>(Sys&, float*, int, int);
 template int bt_he2hb<zd>(Sys&, zd*, int, int);
 
 }  // namespace gev

@@ -86,6 +86,17 @@ __global__ void k_copy2d(int m, int n, const T* __restrict__ src, long long lds,
   }
 }
 
+template <class TA, class TB>
+__global__ void k_convert2d(int m, int n, const TA* __restrict__ src, long long lds, TB* __restrict__ dst,
+                            long long ldd) {
+  const long long total = (long long)m * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(t % m), j = (int)(t / m);
+    dst[i + j * ldd] = (TB)src[i + j * lds];
+  }
+}
+
 // One block per column: the entry of largest modulus (first index on ties) becomes real positive.
 template <class T>
 __global__ void k_normalize_phase(int n, T* C, long long ldc) {
@@ -179,6 +190,19 @@ template <class T> int copy2d(Sys& s, int m, int n, const T* src, long long lds,
   k_copy2d<T><<<blocks, 256, 0, s.stream>>>(m, n, src, lds, dst, ldd);
   return last_error();
 }
+template <class TA, class TB>
+int convert2d(Sys& s, int m, int n, const TA* src, long long lds, TB* dst, long long ldd) {
+  if (m <= 0 || n <= 0) return 0;
+  long long total = (long long)m * n;
+  unsigned blocks = cdiv(total, 256);
+  if (blocks > 16u * s.sms) blocks = 16u * s.sms;
+  GEV_COUNT(s);
+  k_convert2d<TA, TB><<<blocks, 256, 0, s.stream>>>(m, n, src, lds, dst, ldd);
+  return last_error();
+}
+template int convert2d<double, float>(Sys&, int, int, const double*, long long, float*, long long);
+template int convert2d<float, double>(Sys&, int, int, const float*, long long, double*, long long);
+
 template <class T> int normalize_phase(Sys& s, int n, int k, T* C, int ldc) {
   if (n <= 0 || k <= 0) return 0;
   GEV_COUNT(s);
@@ -203,6 +227,7 @@ int sync_status(Sys& s) {
   template int normalize_phase<T>(Sys&, int, int, T*, int);
 GEV_INST(double)
 GEV_INST(zd)
+GEV_INST(float)
 #undef GEV_INST
 
 }  // namespace gev
