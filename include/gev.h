@@ -80,6 +80,9 @@ typedef struct {
   size_t workspace_limit;/* bytes; 0 = no limit */
   int timing;            /* 1: record per-step times into gev_report.ms; 2: also time every GEMM
                             launch (CUDA events) and sum its algorithmic flops (gemm_ms/gemm_flops) */
+  int fp64_emulation;    /* FP64 matrix products (real data): 1 = formed exactly from BF16 digit
+                            planes on the tensor cores (error below 2^-52 of the row/column scale),
+                            0 = native FP64 DMMA, -1 = automatic (on for GEV_MIXED, off for GEV_PLAIN) */
 } gev_opts;
 
 typedef struct {

@@ -1,5 +1,5 @@
 /*
- * gev_kernels.h -- the FP32 matrix product used by the mixed-precision form, as a C entry point.
+ * gev_kernels.h -- the matrix products of the mixed-precision form, as C entry points.
  *
  * The mixed form runs its reduction and back-transforms in FP32 (the single/double-precision pattern
  * named in the section "Future Plans and Challenges").  Its products are formed on the tensor cores
@@ -26,6 +26,19 @@ extern "C" {
 int gev_gemm_f32(int M, int N, int K, int ta, int tb, float alpha, const float* A, int lda,
                  const float* B, int ldb, float beta, float* C, int ldc, int engine, void* stream,
                  int* status_dev);
+
+/* C = alpha op(A) op(B) + beta C in FP64 (real), column-major device pointers, current device.
+     engine      : 0 = native FP64 tensor path (DMMA), 1 = emulated on the BF16 tensor cores: every row
+                   of op(A) / column of op(B) is scaled by a power of two, split into 8 exact 7-bit
+                   digit planes stored as BF16, and the digit products with p + q <= 9 are summed
+                   exactly per 128-deep chunk of K for the leading diagonals, so the error stays below
+                   about 2^-52 (|A| |B|)_ij
+     status_dev  : device pointer to 16 ints (a bounded wait that expired writes status_dev[1])
+     scratch_dev : engine 1: device pointer to 2 * (max(M, N) + 8) ints of scratch
+   Returns 0, -i for an invalid i-th argument, or GEV_ERR_CUDA.  Allocates nothing. */
+int gev_gemm_f64(int M, int N, int K, int ta, int tb, double alpha, const double* A, int lda,
+                 const double* B, int ldb, double beta, double* C, int ldc, int engine, void* stream,
+                 int* status_dev, int* scratch_dev);
 
 #ifdef __cplusplus
 }

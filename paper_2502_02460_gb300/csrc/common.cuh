@@ -128,6 +128,7 @@ template <class T> void gemm(Sys& s, GemmP<T> p);
 template <class TI, class TO> void gemm32(Sys& s, const GemmP<TI>& p, TO* C, float alpha, float beta);
 template <> void gemm<float>(Sys& s, GemmP<float> p);  // FP32: gemm32<float, float>
 void gemm_account(Sys& s, int* calls, double* ms, double* flops);
+void gemm_f64_emulated(Sys& s, const GemmP<double>& p);
 template <class T> GemmP<T> gp(int M, int N, int K, int ta, int tb, T alpha, const T* A, long long lda,
                                const T* B, long long ldb, T beta, T* C, long long ldc) {
   GemmP<T> p{};
@@ -181,6 +182,8 @@ struct Sys {
   double* R2 = nullptr;
   double* R3 = nullptr;
   void* sub = nullptr;    // mixed form: handle of the k x k Rayleigh-Ritz pencil (gev_sys*)
+  int emu_fp64 = 0;       // 1: real FP64 GEMMs formed on the tensor cores (ozaki.cu)
+  int* ozws = nullptr;    // exponent scratch of the emulated FP64 GEMM (2 (n + 8) ints)
   int sub_n = 0;
   void* panelws = nullptr;  // cooperative panel partial sums
   size_t panelws_bytes = 0;

@@ -258,6 +258,16 @@ template <class T> void gemm(Sys& s, GemmP<T> p) {
     s.gemm_fl[s.gemm_used] = algorithmic_flops(p);
     cudaEventRecord(ev0, s.stream);
   }
+  if constexpr (!is_cx<T>::value) {
+    if (s.emu_fp64) {  // FP64 product from BF16 digit planes on the tensor cores
+      gemm_f64_emulated(s, p);
+      if (s.account) {
+        cudaEventRecord(ev1, s.stream);
+        ++s.gemm_used;
+      }
+      return;
+    }
+  }
   dim3 grid(cdiv(p.M, BM), cdiv(p.N, BN), 1);
   long long tiles = (long long)grid.x * grid.y;
   if (p.c_lower) tiles = (tiles + grid.x) / 2;

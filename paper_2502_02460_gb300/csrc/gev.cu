@@ -62,6 +62,7 @@ size_t carve(Sys& s, char* base) {
   size_t panel = (size_t)4096 * (2 * b + 8) * es * 2;
   size_t opanel = L.add(panel);
   size_t ost = L.add(sizeof(int) * ST_COUNT);
+  size_t ooz = L.add(sizeof(int) * 2 * (n + 16));
   const bool mixed = s.opts.prec == GEV_MIXED;
   size_t oR1 = L.add(mixed ? n * n * 8 : 8), oR2 = L.add(mixed ? n * n * 8 : 8), oR3 = L.add(mixed ? n * n * 8 : 8);
   if (base) {
@@ -78,6 +79,7 @@ size_t carve(Sys& s, char* base) {
     s.prog = (int*)(base + oprog);
     s.panelws = base + opanel; s.panelws_bytes = panel;
     s.status = (int*)(base + ost);
+    s.ozws = (int*)(base + ooz);
     s.R1 = (double*)(base + oR1);
     s.R2 = (double*)(base + oR2);
     s.R3 = (double*)(base + oR3);
@@ -96,6 +98,7 @@ void fill_defaults(gev_opts* o) {
   o->refine_max_iter = 4;
   o->workspace_limit = 0;
   o->timing = 0;
+  o->fp64_emulation = -1;
 }
 
 int init_sys(Sys& s, int n, int dtype, const gev_opts* opts) {
@@ -108,6 +111,8 @@ int init_sys(Sys& s, int n, int dtype, const gev_opts* opts) {
   s.nb = 64;
   if (s.opts.panel_nb > 0 && s.opts.panel_nb < 64) s.nb = (s.opts.panel_nb + 7) / 8 * 8;
   s.b = pick_band(n, s.opts.band_b);
+  s.emu_fp64 = s.opts.fp64_emulation < 0 ? (s.opts.prec == GEV_MIXED ? 1 : 0) : (s.opts.fp64_emulation ? 1 : 0);
+  if (dtype == GEV_C128) s.emu_fp64 = 0;
   return 0;
 }
 

@@ -194,6 +194,7 @@ int solve_mixed(Sys& s, const double* H, int ldh, const double* S, int lds, int 
     o.timing = 0;
     o.workspace_limit = 0;
     o.band_b = 0;
+    o.fp64_emulation = s.emu_fp64;  // the Ritz pencil's products use the same FP64 engine
     gev_sys* h = nullptr;
     const int rc = gev_setup(&h, k, GEV_F64, &o);
     if (rc) return rc;
