@@ -28,17 +28,22 @@ int gev_gemm_f32(int M, int N, int K, int ta, int tb, float alpha, const float* 
                  int* status_dev);
 
 /* C = alpha op(A) op(B) + beta C in FP64 (real), column-major device pointers, current device.
-     engine      : 0 = native FP64 tensor path (DMMA), 1 = emulated on the BF16 tensor cores: every row
-                   of op(A) / column of op(B) is scaled by a power of two, split into 8 exact 7-bit
-                   digit planes stored as BF16, and the digit products with p + q <= 9 are summed
-                   exactly per 128-deep chunk of K for the leading diagonals, so the error stays below
-                   about 2^-52 (|A| |B|)_ij
-     status_dev  : device pointer to 16 ints (a bounded wait that expired writes status_dev[1])
-     scratch_dev : engine 1: device pointer to 2 * (max(M, N) + 8) ints of scratch
-   Returns 0, -i for an invalid i-th argument, or GEV_ERR_CUDA.  Allocates nothing. */
+     engine        : 0 = native FP64 tensor path (DMMA), 1 = emulated on the BF16 tensor cores: every
+                     row of op(A) / column of op(B) is scaled by a power of two, split into 8 exact
+                     balanced 7-bit digit planes stored as BF16, and the digit products with
+                     p + q <= 9 are summed on the tensor cores (exactly, per 512-deep chunk of K, for
+                     p + q <= 7), so the error stays below about 2^-50 (|A| |B|)_ij
+     status_dev    : device pointer to 16 ints (a bounded wait that expired writes status_dev[1])
+     scratch_dev   : engine 1: device scratch of scratch_bytes >= gev_gemm_f64_scratch_bytes(M, N, K)
+                     (digit planes: about 16 (M + N) min(K, 32768) bytes, plus split-K partials)
+   Returns 0, -i for an invalid i-th argument, or GEV_ERR_CUDA.  Allocates nothing.  An Inf or NaN
+   entry of op(A) / op(B) makes every output of its row / column NaN (engine 1). */
 int gev_gemm_f64(int M, int N, int K, int ta, int tb, double alpha, const double* A, int lda,
                  const double* B, int ldb, double beta, double* C, int ldc, int engine, void* stream,
-                 int* status_dev, int* scratch_dev);
+                 int* status_dev, void* scratch_dev, size_t scratch_bytes);
+
+/* Bytes of scratch gev_gemm_f64 needs for engine 1 (0 for negative sizes). */
+size_t gev_gemm_f64_scratch_bytes(int M, int N, int K);
 
 #ifdef __cplusplus
 }

@@ -129,6 +129,7 @@ template <class TI, class TO> void gemm32(Sys& s, const GemmP<TI>& p, TO* C, flo
 template <> void gemm<float>(Sys& s, GemmP<float> p);  // FP32: gemm32<float, float>
 void gemm_account(Sys& s, int* calls, double* ms, double* flops);
 void gemm_f64_emulated(Sys& s, const GemmP<double>& p);
+size_t gemm_f64_emulated_scratch(int M, int N, int K);  // bytes of s.ozws for an M x N x K product
 template <class T> GemmP<T> gp(int M, int N, int K, int ta, int tb, T alpha, const T* A, long long lda,
                                const T* B, long long ldb, T beta, T* C, long long ldc) {
   GemmP<T> p{};
@@ -183,7 +184,8 @@ struct Sys {
   double* R3 = nullptr;
   void* sub = nullptr;    // mixed form: handle of the k x k Rayleigh-Ritz pencil (gev_sys*)
   int emu_fp64 = 0;       // 1: real FP64 GEMMs formed on the tensor cores (ozaki.cu)
-  int* ozws = nullptr;    // exponent scratch of the emulated FP64 GEMM (2 (n + 8) ints)
+  void* ozws = nullptr;   // emulated FP64 GEMM: exponents + digit planes (gemm_f64_emulated_scratch)
+  size_t ozws_bytes = 0;
   int sub_n = 0;
   void* panelws = nullptr;  // cooperative panel partial sums
   size_t panelws_bytes = 0;

@@ -62,7 +62,8 @@ size_t carve(Sys& s, char* base) {
   size_t panel = (size_t)4096 * (2 * b + 8) * es * 2;
   size_t opanel = L.add(panel);
   size_t ost = L.add(sizeof(int) * ST_COUNT);
-  size_t ooz = L.add(sizeof(int) * 2 * (n + 16));
+  const size_t ozb = s.emu_fp64 ? gemm_f64_emulated_scratch((int)n, (int)n, (int)n) : 0;
+  size_t ooz = L.add(ozb);
   const bool mixed = s.opts.prec == GEV_MIXED;
   size_t oR1 = L.add(mixed ? n * n * 8 : 8), oR2 = L.add(mixed ? n * n * 8 : 8), oR3 = L.add(mixed ? n * n * 8 : 8);
   if (base) {
@@ -79,7 +80,8 @@ size_t carve(Sys& s, char* base) {
     s.prog = (int*)(base + oprog);
     s.panelws = base + opanel; s.panelws_bytes = panel;
     s.status = (int*)(base + ost);
-    s.ozws = (int*)(base + ooz);
+    s.ozws = ozb ? base + ooz : nullptr;
+    s.ozws_bytes = ozb;
     s.R1 = (double*)(base + oR1);
     s.R2 = (double*)(base + oR2);
     s.R3 = (double*)(base + oR3);

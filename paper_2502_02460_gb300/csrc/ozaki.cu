@@ -1,25 +1,31 @@
-// FP64 GEMM emulated on the BF16 tensor cores (tcgen05), for the FP64 stages of the mixed form.
+// FP64 GEMM emulated on the BF16 tensor cores (tcgen05), for the FP64 matrix products.
 //
 // GB300 executes FP64 at ~1 TFLOP/s (DMMA and DFMA alike) but BF16 at ~1.9 PFLOP/s, so an FP64
 // product is formed from exact BF16 pieces (an error-free splitting in the manner of Ozaki, Ogita,
 // Oishi and Rump):
 //
-//   row i of op(A) is scaled by 2^-E_i, column j of op(B) by 2^-F_j (E, F: exponents just above the
-//   largest magnitude), so every scaled entry x lies in (-1, 1);  x = sum_{p=1..8} a_p 2^-7p with
-//   integer digits |a_p| <= 127 taken from the bits of x (integer arithmetic only, truncated below
-//   2^-56);  a_p 2^-7p is stored as BF16, exactly.
+//   row i of op(A) is scaled by 2^-(E_i+1), column j of op(B) by 2^-(F_j+1) (E, F: the smallest
+//   exponents with |x| < 2^E over the row / column), so every scaled entry lies in (-1/2, 1/2);
+//   X = x 2^(55-E) truncated to an integer (|X| < 2^55) is written in balanced radix 2^7,
+//   X = sum_{p=1..8} a_p 2^(56-7p) with integer digits |a_p| <= 64 (integer arithmetic only), and
+//   a_p 2^-7p is stored as BF16, exactly.
 //
-//   A B = 2^(E_i+F_j) sum_{p,q} (a_p 2^-7p)(b_q 2^-7q); pairs with p + q >= 10 (< 2^-56 relative)
-//   are dropped.  For d = p + q <= 7 the products of one diagonal d are integers times 2^-7d below
-//   2^14: summed over a K chunk of 128 with at most 6 pairs they stay below 2^24, so the FP32
-//   tensor-memory accumulator holds them exactly; after each chunk these exact sums are added to
-//   one FP64 accumulator per output in registers (6 additions per 128 of K: fewer roundings than an
-//   FP64 dot product of length K).  The diagonals d = 8, 9 share one FP32 accumulator over all of
-//   K; its roundings stay near 2^-51 of the result.
+//   A B = 2^(E_i+F_j+2) sum_{p,q} (a_p 2^-7p)(b_q 2^-7q); pairs with p + q >= 10 (each below 2^-58
+//   of the scale) are dropped.  For d = p + q <= 7 the products of diagonal d are integers times
+//   2^-7d of magnitude <= 2^12; summed over a K chunk of 512 with at most 6 pairs they stay below
+//   2^24, so the FP32 tensor-memory accumulator holds them exactly.  After each chunk the six exact
+//   sums are added, as integers in units of 2^-49, to one 64-bit integer accumulator per output
+//   (exact; integer operations are cheap on GB300 while FP64 additions are not).  The diagonals
+//   d = 8, 9 share one FP32 accumulator over all of K; its roundings stay near 2^-51 of the scale.
 //
-// CTA tile 128 x 64 (TMEM: 6 exact accumulators + 1 shared, 64 columns each), 128 threads; the 8
-// digit planes of the 128 x 64 A slice and the 64 x 64 B slice occupy 192 KB of shared memory
-// (canonical K-major layout without swizzle, as in tc_gemm.cu).  Every mbarrier wait is bounded.
+// Data flow: a split pass writes the 8 digit planes of op(A) and op(B) to global memory in the
+// order the MMAs consume them (one 16-deep k-slice of a 128-row A tile = 8 planes x 4 KB,
+// contiguous; of a 64-column B tile = 8 x 2 KB), so the GEMM kernel moves them with plain bulk
+// asynchronous copies into a 4-stage shared-memory ring.  Warp roles: warp 8 issues the copies,
+// warp 9 issues the 36 MMAs per slice (tcgen05, accumulators in TMEM: 6 exact diagonals + 1
+// shared, 64 columns each), warps 0-7 (one TMEM lane per output row, half of its 64 columns
+// each) drain the exact accumulators at every chunk end and write C.  Every mbarrier wait is bounded; on expiry the kernel records
+// ST_TIMEOUT, waits (bounded) for its copies and MMAs in flight, frees TMEM and returns.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -31,23 +37,38 @@ namespace gev {
 
 namespace {
 
-constexpr int OM = 128, ON = 64, OK_ = 64, NTH = 128, NSLICE = 8, DMAX = 9, DEXACT = 7;
-constexpr int A_PLANE = OM * OK_ * 2;  // 16 KB
-constexpr int B_PLANE = ON * OK_ * 2;  // 8 KB
-constexpr int SMEM_OZ = NSLICE * (A_PLANE + B_PLANE) + 1024;
+constexpr int OM = 128, ON = 64, KS = 16, NSTAGE = 4, NSLICE = 8, DMAX = 9, DEXACT = 7;
+constexpr int CHUNK = 32;                  // k-slices per exact chunk (512 of K)
+constexpr int KMAX = 32768;                // K per launch: the int64 sums stay below 2^63
+constexpr int A_TILE = OM * KS * 2;        // one plane of a 128 x 16 slice: 4 KB
+constexpr int B_TILE = ON * KS * 2;        // one plane of a 64 x 16 slice: 2 KB
+constexpr int A_STAGE = NSLICE * A_TILE;   // 32 KB
+constexpr int B_STAGE = NSLICE * B_TILE;   // 16 KB
+constexpr int STAGE = A_STAGE + B_STAGE;   // 48 KB
+constexpr int SMEM_OZ = NSTAGE * STAGE + 1024;
+constexpr int NEPI_W = 8;                  // epilogue warps: TMEM lanes 32 (w % 4), columns 32 (w / 4)
+constexpr int HC = ON / 2;                  // output columns per epilogue thread
+constexpr int NTH = 32 * (NEPI_W + 2);      // + copy warp 8 + MMA warp 9
 constexpr int TMEM_COLS_OZ = 512;
+constexpr int SHARED_SLOT = DEXACT - 1;    // TMEM slot of d = 8, 9; exact d at slot d - 2
+constexpr int GROUP_M = 16;                // raster: 16 row tiles share their B slices in L2
+constexpr int EXP_BAD = 1 << 20;           // exponent marking a non-finite entry
+constexpr int EXP_ZERO = -4000;            // exponent of an all-zero vector
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ int toff(int r, int k) {
-  return ((r >> 3) * (OK_ / 8) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2;
+// byte offset of element (r, k) in a K-major 16-deep plane tile: 8 x 8 core matrices of 16-byte
+// rows, the two k-halves adjacent (leading offset 128 B), 8-row groups 256 B apart
+__host__ __device__ __forceinline__ int toff(int r, int k) {
+  return ((r >> 3) * 2 + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2;
 }
 
 __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
-  const uint64_t lbo = 128, sbo = (OK_ / 8) * 128;
+  const uint64_t lbo = 128, sbo = 256;
   return (uint64_t)((addr & 0x3FFFF) >> 4) | ((lbo >> 4) << 16) | ((sbo >> 4) << 32) | ((uint64_t)1 << 46);
 }
 
+// instruction descriptor: D = F32, A = B = BF16, both K-major, N = 64, M = 128
 __host__ __device__ constexpr uint32_t idesc_oz() {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(ON >> 3) << 17) | ((uint32_t)(OM >> 4) << 24);
 }
@@ -59,106 +80,229 @@ __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t
       "l"(a), "l"(b), "r"(id), "r"(acc));
 }
 
-__device__ __forceinline__ bool bar_wait(uint32_t mbar, uint32_t parity) {
+__device__ __forceinline__ void commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar)
+               : "memory");
+}
+
+__device__ __forceinline__ bool try_wait(uint32_t mbar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(mbar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait; gives up early once another role has recorded an error in *err
+__device__ __forceinline__ bool bar_wait(uint32_t mbar, uint32_t parity, volatile int* err) {
   for (long long it = 0; it < kSpinLimit; ++it) {
-    uint32_t ok;
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(mbar), "r"(parity)
-        : "memory");
-    if (ok) return true;
-    __nanosleep(20);
+    if (try_wait(mbar, parity)) return true;
+    if ((it & 255) == 255 && *err) return false;
+    __nanosleep(32);
   }
   return false;
 }
 
-// exponent E with |x| < 2^E for a finite x != 0 (0 for x == 0)
+// bounded wait without the early exit (draining after an error)
+__device__ __forceinline__ bool bar_wait_plain(uint32_t mbar, uint32_t parity) {
+  for (long long it = 0; it < kSpinLimit; ++it) {
+    if (try_wait(mbar, parity)) return true;
+    __nanosleep(32);
+  }
+  return false;
+}
+
+// exponent e with |x| < 2^e for a finite x != 0; EXP_ZERO for 0, EXP_BAD for Inf / NaN
 __device__ __forceinline__ int exp_above(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const int be = (int)((b >> 52) & 0x7FF);
-  if (be == 0) return (b << 1) ? -1022 : -100000;  // subnormal / zero
-  return be - 1022;  // |x| < 2^(be - 1023 + 1)
+  if (be == 0x7FF) return EXP_BAD;
+  if (be == 0) return (b << 1) ? -1022 : EXP_ZERO;
+  return be - 1022;
 }
 
-// per-row exponents of op(A) (mask applied): one thread per row
-__global__ void k_row_exp(int M, int K, const double* A, long long lda, int ta, int tri, int* E) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= M) return;
-  int e = -100000;
-  const int k0 = (tri == 2) ? min(i, K) : 0, k1 = (tri == 1) ? min(i + 1, K) : K;
-  for (int k = k0; k < k1; ++k) e = max(e, exp_above(ta == 0 ? A[i + k * lda] : A[k + i * lda]));
-  E[i] = (e == -100000) ? 0 : e;
+__device__ __forceinline__ bool kept(int keep, long long r, long long k) {
+  return keep == 0 || (keep == 1 ? k <= r : k >= r);
 }
 
-// per-column exponents of op(B) (mask applied): one thread per column
-__global__ void k_col_exp(int N, int K, const double* B, long long ldb, int tb, int tri, int* F) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= N) return;
-  int e = -100000;
-  const int k0 = (tri == 1) ? min(j, K) : 0, k1 = (tri == 2) ? min(j + 1, K) : K;
-  for (int k = k0; k < k1; ++k) e = max(e, exp_above(tb == 0 ? B[k + j * ldb] : B[j + k * ldb]));
-  F[j] = (e == -100000) ? 0 : e;
+// E[r] = max exponent over the kept entries of vector r: element k of vector r at X[r sr + k sk]
+// (absolute index k + koff for the mask; keep 1: k <= r, 2: k >= r).  E holds a very negative
+// value on entry (atomicMax).  Block 32 x 8; grid.y covers K in slices of 1024.
+__global__ void k_vec_exp(int R, int K, int koff, const double* X, long long sr, long long sk, int keep, int* E) {
+  const int k_lo = blockIdx.y * 1024, k_hi = min(K, k_lo + 1024);
+  if (sr == 1) {  // the vectors run across the threads of a warp
+    const int r = blockIdx.x * 32 + threadIdx.x;
+    if (r >= R) return;
+    int e = EXP_ZERO;
+    for (int k = k_lo + threadIdx.y; k < k_hi; k += 8)
+      if (kept(keep, r, (long long)k + koff)) e = max(e, exp_above(X[r + (long long)k * sk]));
+    if (e != EXP_ZERO) atomicMax(&E[r], e);
+  } else {  // each vector is contiguous: a warp reads it
+    const int r = blockIdx.x * 8 + threadIdx.y;
+    if (r >= R) return;  // uniform across the warp
+    int e = EXP_ZERO;
+    for (int k = k_lo + threadIdx.x; k < k_hi; k += 32)
+      if (kept(keep, r, (long long)k + koff)) e = max(e, exp_above(X[(long long)r * sr + k]));
+    e = __reduce_max_sync(0xffffffffu, e);
+    if (threadIdx.x == 0 && e != EXP_ZERO) atomicMax(&E[r], e);
+  }
 }
 
-// the 8 digit planes of x * 2^-E, as BF16 with their scale 2^-7p
-__device__ __forceinline__ void split_digits(double x, int E, unsigned char* planes, int plane_bytes, int off) {
+__device__ __forceinline__ int clamp_exp(int e) { return e < -1100 ? EXP_ZERO : e; }
+
+// the balanced radix-2^7 digits of x 2^(55-E) (|x| < 2^E), as BF16 bit patterns of a_p 2^-7p
+__device__ __forceinline__ void digits(double x, int E, uint16_t out[NSLICE]) {
   const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
   const int be = (int)((bits >> 52) & 0x7FF);
-  unsigned long long X = 0;
-  if (be != 0 || (bits << 1) != 0) {
+  long long X = 0;
+  if (E < EXP_BAD && (be != 0 || (bits << 1) != 0)) {
     unsigned long long m = bits & 0xFFFFFFFFFFFFFull;
     int ex;
     if (be == 0) { ex = -1022; } else { m |= (1ull << 52); ex = be - 1023; }
-    const int s = ex - E + 4;  // X = |x| 2^(56-E) = m 2^(ex - 52 + 56 - E)
-    if (s >= 0) X = m << s;            // s <= 3 since |x| < 2^E
-    else if (s > -64) X = m >> (-s);   // digits below 2^-56 are dropped
+    const int s = ex + 3 - E;  // X = m 2^(ex - 52 + 55 - E); s <= 2 since |x| < 2^E
+    unsigned long long u = 0;
+    if (s >= 0) u = m << s;
+    else if (s > -64) u = m >> (-s);  // bits below 2^-55 of the scale are dropped
+    X = (bits >> 63) ? -(long long)u : (long long)u;
   }
-  const bool neg = (bits >> 63) != 0;
 #pragma unroll
   for (int p = 1; p <= NSLICE; ++p) {
-    const int dig = (int)((X >> (56 - 7 * p)) & 127ull);
-    float v = __int2float_rn(neg ? -dig : dig);
-    v = ldexpf(v, -7 * p);  // exact: a power-of-two scale of a 7-bit integer
-    *reinterpret_cast<__nv_bfloat16*>(planes + (p - 1) * plane_bytes + off) = __float2bfloat16_rn(v);
+    const int sh = 56 - 7 * p;
+    long long a;
+    if (sh > 0) a = (X + (1ll << (sh - 1))) >> sh;  // nearest integer to X 2^-sh: |a| <= 64
+    else a = X;
+    X -= a * (1ll << sh);
+    const float v = (float)a * __int_as_float((127 - 7 * p) << 23);  // a 2^-7p, exact
+    out[p - 1] = __bfloat16_as_ushort(__float2bfloat16_rn(v));         // exact: |a| <= 64
+  }
+}
+
+// Digit planes of one operand: vector r (a row of op(A) or a column of op(B)), element k, rows
+// padded to RT tiles of TR, k to KT slices of 16.  One thread per (r, 8 consecutive k): it writes
+// 16 bytes to each of the 8 planes of tile (r / TR, k / 16).
+__global__ void k_split(int R, int K, int koff, const double* X, long long sr, long long sk, int keep,
+                        const int* E, int TR, int RT, int KT, unsigned char* out) {
+  const long long Rp = (long long)RT * TR, G = 2LL * KT;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= Rp * G) return;
+  long long r, g;
+  if (sr == 1) { r = t % Rp; g = t / Rp; } else { g = t % G; r = t / G; }
+  const int Er = (r < R) ? clamp_exp(E[r]) : EXP_ZERO;
+  uint16_t dg[8][NSLICE];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const long long k = g * 8 + q;
+    double v = 0.0;
+    if (r < R && k < K && kept(keep, r, k + koff)) v = X[r * sr + k * sk];
+    digits(v, Er, dg[q]);
+  }
+  const long long rt = r / TR, kt = g >> 1;
+  const int tile_bytes = TR * KS * 2;
+  unsigned char* base =
+      out + ((rt * KT + kt) * NSLICE) * (long long)tile_bytes + toff((int)(r % TR), (int)(g & 1) * 8);
+#pragma unroll
+  for (int p = 0; p < NSLICE; ++p) {
+    uint4 v;
+    v.x = (uint32_t)dg[0][p] | ((uint32_t)dg[1][p] << 16);
+    v.y = (uint32_t)dg[2][p] | ((uint32_t)dg[3][p] << 16);
+    v.z = (uint32_t)dg[4][p] | ((uint32_t)dg[5][p] << 16);
+    v.w = (uint32_t)dg[6][p] | ((uint32_t)dg[7][p] << 16);
+    *reinterpret_cast<uint4*>(base + (long long)p * tile_bytes) = v;
   }
 }
 
 struct OzP {
-  int M, N, K, ta, tb, tri_a, tri_b, c_lower;
+  int M, N, K, koff, c_lower, tri_a, tri_b;
+  int MT, NT, KT, ksplit;
   double alpha, beta;
-  const double* A;
-  long long lda;
-  const double* B;
-  long long ldb;
   double* C;
   long long ldc;
+  double* ws;  // split-K partials (ksplit > 1): ws[z M N + i + j M]
+  const unsigned char* Ap;
+  const unsigned char* Bp;
   const int* E;
   const int* F;
   int* status;
 };
 
+// an exact FP32 chunk sum (a multiple of 2^-49 below 2^8 in magnitude) in units of 2^-49
+__device__ __forceinline__ long long units49(uint32_t b) {
+  const uint32_t e = (b >> 23) & 0xFF;
+  const unsigned long long m = (unsigned long long)((b & 0x7FFFFFu) | 0x800000u) << 40;
+  unsigned long long t;
+  asm("shr.b64 %0, %1, %2;" : "=l"(t) : "l"(m), "r"(141u - e));  // m 2^(e - 101); 0 for e = 0
+  return (b >> 31) ? -(long long)t : (long long)t;
+}
+
+// x 2^e without a library call (two exact power-of-two factors cover |e| <= 2046)
+__device__ __forceinline__ double pow2(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
+__device__ __forceinline__ double scale2(double x, int e) {
+  if (e >= -1022 && e <= 1023) return x * pow2(e);
+  e = max(-2044, min(2046, e));
+  const int h = e / 2;
+  return (x * pow2(h)) * pow2(e - h);
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+
 __global__ void __launch_bounds__(NTH, 1) ozaki_kernel(OzP p) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int m0 = blockIdx.x * OM, n0 = blockIdx.y * ON;
+  // grouped raster: GROUP_M row tiles sweep the column tiles together
+  const int per_group = GROUP_M * p.NT;
+  const int first = (blockIdx.x / per_group) * GROUP_M;
+  const int gm = min(p.MT - first, GROUP_M);
+  const int within = blockIdx.x % per_group;
+  const int mt = first + within % gm, nt = within / gm;
+  const int m0 = mt * OM, n0 = nt * ON;
   if (p.c_lower && n0 > m0 + OM - 1) return;
-  int kb = 0, ke = p.K;
-  if (p.tri_a == 1) ke = min(ke, m0 + OM);
-  else if (p.tri_a == 2) kb = max(kb, m0);
-  if (p.tri_b == 1) kb = max(kb, n0);
-  else if (p.tri_b == 2) ke = min(ke, n0 + ON);
-  kb = kb / OK_ * OK_;
-  unsigned char* Ap = smem;                                // 8 planes x 16 KB
-  unsigned char* Bp = smem + NSLICE * A_PLANE;              // 8 planes x 8 KB
-  unsigned char* ctrl = smem + NSLICE * (A_PLANE + B_PLANE);
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(ctrl);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(ctrl + 64);
-  int* flag = reinterpret_cast<int*>(ctrl + 128);
+  // k-slices holding non-zero products for this tile (absolute k = local k + koff)
+  long long kb = 0, ke = p.K;
+  if (p.tri_a == 1) ke = std::min<long long>(ke, (long long)m0 + OM - p.koff);
+  else if (p.tri_a == 2) kb = std::max<long long>(kb, (long long)m0 - p.koff);
+  if (p.tri_b == 1) kb = std::max<long long>(kb, (long long)n0 - p.koff);
+  else if (p.tri_b == 2) ke = std::min<long long>(ke, (long long)n0 + ON - p.koff);
+  int s_lo = (int)(kb / KS), s_hi = (int)(ke > 0 ? (ke + KS - 1) / KS : 0);
+  if (s_hi < s_lo) s_hi = s_lo;
+  if (p.ksplit > 1) {  // this CTA's share of the slices
+    const int tot = s_hi - s_lo, z = blockIdx.y;
+    const int a = s_lo + (int)((long long)tot * z / p.ksplit);
+    const int b = s_lo + (int)((long long)tot * (z + 1) / p.ksplit);
+    s_lo = a;
+    s_hi = b;
+  }
+  const int nst = s_hi - s_lo, nchunk = (nst + CHUNK - 1) / CHUNK;
+
+  unsigned char* ctrl = smem + NSTAGE * STAGE;
+  uint64_t* full = reinterpret_cast<uint64_t*>(ctrl);  // [NSTAGE]: slice landed
+  uint64_t* empty = full + NSTAGE;                      // [NSTAGE]: slice consumed by the MMAs
+  uint64_t* cfull = empty + NSTAGE;                     // chunk accumulated
+  uint64_t* cempty = cfull + 1;                         // chunk drained by the epilogue warps
+  uint64_t* done = cempty + 1;                          // all MMAs complete
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(ctrl + 256);
+  volatile int* err = reinterpret_cast<volatile int*>(ctrl + 320);
+  int* issued = reinterpret_cast<int*>(ctrl + 384);
+  int* consumed = reinterpret_cast<int*>(ctrl + 448);
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(su32(mbar)));
+    for (int s = 0; s < NSTAGE; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(su32(&full[s])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(su32(&empty[s])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(su32(cfull)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(su32(cempty)), "r"(NEPI_W));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(su32(done)));
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-    *flag = 0;
+    *err = 0;
+    *issued = 0;
+    *consumed = 0;
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(su32(tslot)),
@@ -169,133 +313,150 @@ __global__ void __launch_bounds__(NTH, 1) ozaki_kernel(OzP p) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = *tslot;
-  const uint32_t id = idesc_oz();
-  // TMEM accumulators: exact diagonals d = 2..7 at columns (d-2)*64, the shared one at 6*64
-  constexpr int SHARED_SLOT = DEXACT - 1;
-  double acc[ON];
+
+  if (warp == NEPI_W) {
+    // ---- copy warp: digit-plane slices into the stage ring
+    if (lane == 0) {
+      const unsigned char* a_src = p.Ap + (long long)mt * p.KT * A_STAGE;
+      const unsigned char* b_src = p.Bp + (long long)nt * p.KT * B_STAGE;
+      for (int s = 0; s < nst; ++s) {
+        const int slot = s % NSTAGE;
+        if (s >= NSTAGE && !bar_wait(su32(&empty[slot]), ((s / NSTAGE) - 1) & 1, err)) {
+          if (!*err) *err = 411;
+          break;
+        }
+        const uint32_t fb = su32(&full[slot]);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb), "r"(STAGE) : "memory");
+        const uint32_t dst = su32(smem + slot * STAGE);
+        const long long kt = s_lo + s;
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+            "l"(a_src + kt * A_STAGE), "r"(A_STAGE), "r"(fb)
+            : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                dst + A_STAGE),
+            "l"(b_src + kt * B_STAGE), "r"(B_STAGE), "r"(fb)
+            : "memory");
+        *issued = s + 1;
+      }
+    }
+  } else if (warp == NEPI_W + 1) {
+    // ---- MMA warp: 36 digit-pair products per 16-deep slice
+    if (lane == 0) {
+      const uint32_t id = idesc_oz();
+      for (int s = 0; s < nst; ++s) {
+        const int slot = s % NSTAGE, c = s / CHUNK;
+        const bool chunk_start = (s % CHUNK) == 0;
+        if (chunk_start && c > 0 && !bar_wait(su32(cempty), (c - 1) & 1, err)) {
+          if (!*err) *err = 412;
+          break;
+        }
+        if (!bar_wait(su32(&full[slot]), (s / NSTAGE) & 1, err)) {
+          if (!*err) *err = 413;
+          break;
+        }
+        *consumed = s + 1;
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const uint32_t a0 = su32(smem + slot * STAGE), b0 = a0 + A_STAGE;
 #pragma unroll
-  for (int c = 0; c < ON; ++c) acc[c] = 0.0;
-  const int row = warp * 32 + lane;  // TMEM lane = tile row owned by this thread
-  const int nsteps = (ke > kb) ? (ke - kb + OK_ - 1) / OK_ : 0;
-  uint32_t phase = 0;
-  bool ok = true;
-  for (int st = 0; st < nsteps && ok; ++st) {
-    const int k0 = kb + st * OK_;
-    // ---- producer: digit planes of the 128 x 64 A slice and the 64 x 64 B slice
-    for (int e = tid; e < OM * OK_; e += NTH) {
-      int r, k;
-      if (p.ta == 0) { r = e % OM; k = e / OM; } else { k = e % OK_; r = e / OK_; }
-      const int gi = m0 + r, gk = k0 + k;
-      double v = 0.0;
-      int E = 0;
-      if (gi < p.M && gk < ke && !((p.tri_a == 1 && gk > gi) || (p.tri_a == 2 && gk < gi))) {
-        v = (p.ta == 0) ? p.A[gi + gk * p.lda] : p.A[gk + gi * p.lda];
-        E = p.E[gi];
-      }
-      split_digits(v, E, Ap, A_PLANE, toff(r, k));
-    }
-    for (int e = tid; e < ON * OK_; e += NTH) {
-      int c, k;
-      if (p.tb == 0) { k = e % OK_; c = e / OK_; } else { c = e % ON; k = e / ON; }
-      const int gj = n0 + c, gk = k0 + k;
-      double v = 0.0;
-      int F = 0;
-      if (gj < p.N && gk < ke && !((p.tri_b == 1 && gk < gj) || (p.tri_b == 2 && gk > gj))) {
-        v = (p.tb == 0) ? p.B[gk + gj * p.ldb] : p.B[gj + gk * p.ldb];
-        F = p.F[gj];
-      }
-      split_digits(v, F, Bp, B_PLANE, toff(c, k));
-    }
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    __syncthreads();
-    // ---- MMAs of this 64-deep slice: 4 k-steps x 36 digit pairs
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      const bool chunk_start = (st & 1) == 0;  // exact diagonals restart every 128 of K
-      const uint32_t a0 = su32(Ap), b0 = su32(Bp);
-      for (int ks = 0; ks < OK_ / 16; ++ks) {
-        const uint32_t koff = ks * 256;
-        bool first_exact[DEXACT + 1] = {true, true, true, true, true, true, true, true};
         for (int pa = 1; pa <= NSLICE; ++pa) {
+#pragma unroll
           for (int qb = 1; qb + pa <= DMAX; ++qb) {
             const int d = pa + qb;
-            int slot, en;
-            if (d <= DEXACT) {
-              slot = d - 2;
-              en = (chunk_start && ks == 0 && first_exact[d]) ? 0 : 1;
-              first_exact[d] = false;
-            } else {
-              slot = SHARED_SLOT;
-              en = (st == 0 && ks == 0 && pa == 1 && qb == DEXACT) ? 0 : 1;  // first shared-accumulator MMA
+            int col, en;
+            if (d <= DEXACT) {  // the first pair of diagonal d (pa = 1) restarts it at a chunk start
+              col = (d - 2) * ON;
+              en = (chunk_start && pa == 1) ? 0 : 1;
+            } else {  // the shared slot starts with the first MMA of d = 8 (pa = 1, qb = 7)
+              col = SHARED_SLOT * ON;
+              en = (s == 0 && pa == 1 && qb == DEXACT) ? 0 : 1;
             }
-            mma(tmem + slot * ON, sdesc(a0 + (pa - 1) * A_PLANE + koff), sdesc(b0 + (qb - 1) * B_PLANE + koff), id,
-                en);
+            mma(tmem + col, sdesc(a0 + (pa - 1) * A_TILE), sdesc(b0 + (qb - 1) * B_TILE), id, en);
           }
         }
+        commit(su32(&empty[slot]));
+        if ((s % CHUNK) == CHUNK - 1 || s == nst - 1) commit(su32(cfull));
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(su32(mbar))
-                   : "memory");
-      *flag = bar_wait(su32(mbar), phase) ? 0 : 1;
+      commit(su32(done));
+      if (!bar_wait_plain(su32(done), 0) && !*err) *err = 414;
     }
-    __syncthreads();
-    if (*flag) { ok = false; break; }
-    phase ^= 1;
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    // ---- end of a 128-deep chunk (or of K): move the exact diagonals into the integer accumulators
-    if ((st & 1) == 1 || st == nsteps - 1) {
+  } else {
+    // ---- epilogue warps: drain the exact diagonals per chunk, then write C
+    const int quarter = warp & 3, col0 = (warp >> 2) * HC;
+    const int row = quarter * 32 + lane;
+    const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)col0;
+    long long acc[HC];
+#pragma unroll
+    for (int c = 0; c < HC; ++c) acc[c] = 0;
+    bool good = true;
+    for (int c = 0; c < nchunk; ++c) {
+      if (!bar_wait(su32(cfull), c & 1, err)) {
+        if (!*err) *err = 415;
+        good = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 #pragma unroll
       for (int d = 2; d <= DEXACT; ++d) {
+        uint32_t r0[16], r1[16];
+        tmem_ld16(lane_base + (uint32_t)((d - 2) * ON), r0);
+        tmem_ld16(lane_base + (uint32_t)((d - 2) * ON + 16), r1);
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
-        for (int cb = 0; cb < ON; cb += 16) {
-          uint32_t r[16];
-          const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((d - 2) * ON + cb);
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-              "[%16];\n"
-              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                "=r"(r[15])
-              : "r"(taddr));
-          asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-#pragma unroll
-          for (int q = 0; q < 16; ++q) acc[cb + q] += (double)__uint_as_float(r[q]);  // exact chunk sums
+        for (int q = 0; q < 16; ++q) {
+          acc[q] += units49(r0[q]);
+          acc[16 + q] += units49(r1[q]);
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-      __syncthreads();  // the next chunk's first MMAs overwrite these accumulators
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(su32(cempty)) : "memory");
     }
-  }
-  if (!ok && tid == 0) atomicCAS(&p.status[ST_TIMEOUT], 0, 402);
-  // ---- epilogue: the shared low-order accumulator, then C = alpha 2^(E+F) sum + beta C
-  const bool any = nsteps > 0 && ok;
-  const int gi = m0 + row;
-  const int Ei = (gi < p.M) ? p.E[gi] : 0;
+    const bool any = good && nchunk > 0;
+    const int gi = m0 + row;
+    const int Ei = (any && gi < p.M) ? p.E[gi] : EXP_ZERO;
 #pragma unroll
-  for (int cb = 0; cb < ON; cb += 16) {
-    uint32_t r[16];
-    if (any) {
-      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(SHARED_SLOT * ON + cb);
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-    } else {
+    for (int cb = 0; cb < HC; cb += 16) {
+      uint32_t r[16];
+      if (any) {
+        tmem_ld16(lane_base + (uint32_t)(SHARED_SLOT * ON + cb), r);
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+      } else {
 #pragma unroll
-      for (int q = 0; q < 16; ++q) r[q] = 0u;
-    }
-    if (gi < p.M) {
+        for (int q = 0; q < 16; ++q) r[q] = 0u;
+      }
+      if (gi < p.M) {
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const int gj = n0 + cb + q;
-        if (gj >= p.N || (p.c_lower && gi < gj)) continue;
-        const double s = (any ? acc[cb + q] + (double)__uint_as_float(r[q]) : 0.0);
-        const double v = p.alpha * ldexp(s, Ei + p.F[gj]);
-        double* c = &p.C[gi + gj * p.ldc];
-        *c = (p.beta != 0.0) ? v + p.beta * (*c) : v;
+        for (int q = 0; q < 16; ++q) {
+          const int gj = n0 + col0 + cb + q;
+          if (gj >= p.N || (p.c_lower && gi < gj)) continue;
+          double v = 0.0;
+          if (any) {
+            const int Fj = p.F[gj];
+            if (Ei >= EXP_BAD || Fj >= EXP_BAD) {
+              v = __longlong_as_double(0x7FF8000000000000ll);  // an Inf / NaN entry reached this output
+            } else if (Ei >= -1100 && Fj >= -1100) {
+              const double sum = (double)acc[cb + q] * 0x1p-49 + (double)__uint_as_float(r[q]);
+              v = scale2(sum, Ei + Fj + 2);
+            }
+          }
+          if (p.ksplit > 1) {
+            p.ws[(long long)blockIdx.y * p.M * p.N + gi + (long long)gj * p.M] = v;
+          } else {
+            double* cp = &p.C[gi + gj * p.ldc];
+            const double o = p.alpha * v;
+            *cp = (p.beta != 0.0) ? o + p.beta * (*cp) : o;
+          }
+        }
       }
     }
+  }
+  __syncthreads();
+  if (tid == 0 && *err) {
+    // a wait gave up: let the copies already issued land before the shared memory is released
+    for (int s = *consumed; s < *issued; ++s) bar_wait_plain(su32(&full[s % NSTAGE]), (s / NSTAGE) & 1);
+    atomicCAS(&p.status[ST_TIMEOUT], 0, *err);
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
@@ -303,9 +464,45 @@ __global__ void __launch_bounds__(NTH, 1) ozaki_kernel(OzP p) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS_OZ));
 }
 
+// C = alpha sum_z ws[z] + beta C in a fixed order (deterministic)
+__global__ void k_oz_reduce(int M, int N, int ks, int c_lower, double alpha, const double* ws, double beta,
+                            double* C, long long ldc) {
+  const long long total = (long long)M * N;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % M), j = (int)(t / M);
+    if (c_lower && i < j) continue;
+    double s = 0.0;
+    for (int z = 0; z < ks; ++z) s += ws[(long long)z * total + t];
+    double* c = &C[i + (long long)j * ldc];
+    const double o = alpha * s;
+    *c = (beta != 0.0) ? o + beta * (*c) : o;
+  }
+}
+
+size_t rup(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct OzLayout {
+  size_t Mp, Np, Kp, f_off, a_off, b_off, total;
+};
+
+OzLayout oz_layout(int M, int N, int K) {
+  OzLayout L;
+  L.Mp = rup(std::max(M, 1), OM);
+  L.Np = rup(std::max(N, 1), ON);
+  L.Kp = rup(std::max(std::min(K, KMAX), 1), KS);
+  L.f_off = rup(L.Mp * sizeof(int), 256);
+  L.a_off = L.f_off + rup(L.Np * sizeof(int), 256);
+  L.b_off = L.a_off + L.Mp * L.Kp * 2 * NSLICE;
+  L.total = L.b_off + L.Np * L.Kp * 2 * NSLICE;
+  return L;
+}
+
 }  // namespace
 
-// FP64 GEMM on the tensor cores (real data).  Needs 2 * max(M, N) ints of scratch in s.ozws.
+size_t gemm_f64_emulated_scratch(int M, int N, int K) { return oz_layout(M, N, K).total; }
+
+// FP64 GEMM on the tensor cores (real data); scratch s.ozws of s.ozws_bytes >= gemm_f64_emulated_scratch.
 void gemm_f64_emulated(Sys& s, const GemmP<double>& q) {
   if (q.M <= 0 || q.N <= 0) return;
   static bool attr = false;
@@ -313,25 +510,86 @@ void gemm_f64_emulated(Sys& s, const GemmP<double>& q) {
     cudaFuncSetAttribute((const void*)ozaki_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_OZ);
     attr = true;
   }
-  int* E = s.ozws;
-  int* F = s.ozws + std::max(q.M, q.N) + 8;
-  GEV_COUNT(s);
-  k_row_exp<<<cdiv(q.M, 128), 128, 0, s.stream>>>(q.M, q.K, q.A, q.lda, q.ta, q.tri_a, E);
-  GEV_COUNT(s);
-  k_col_exp<<<cdiv(q.N, 128), 128, 0, s.stream>>>(q.N, q.K, q.B, q.ldb, q.tb, q.tri_b, F);
-  OzP p{};
-  p.M = q.M; p.N = q.N; p.K = q.K; p.ta = q.ta; p.tb = q.tb; p.tri_a = q.tri_a; p.tri_b = q.tri_b;
-  p.c_lower = q.c_lower; p.alpha = q.alpha; p.beta = q.beta; p.A = q.A; p.lda = q.lda; p.B = q.B;
-  p.ldb = q.ldb; p.C = q.C; p.ldc = q.ldc; p.E = E; p.F = F; p.status = s.status;
-  GEV_COUNT(s);
-  ozaki_kernel<<<dim3(cdiv(q.M, OM), cdiv(q.N, ON)), NTH, SMEM_OZ, s.stream>>>(p);
+  const OzLayout L = oz_layout(q.M, q.N, q.K);
+  if (s.ozws == nullptr || L.total > s.ozws_bytes) {  // internal sizing error: fail the call loudly
+    fprintf(stderr, "gev: emulated FP64 GEMM scratch too small (%zu < %zu bytes)\n", s.ozws_bytes, L.total);
+    const int site = 499;
+    if (s.status) cudaMemcpyAsync(s.status + ST_TIMEOUT, &site, sizeof(int), cudaMemcpyHostToDevice, s.stream);
+    cudaStreamSynchronize(s.stream);
+    return;
+  }
+  unsigned char* base = static_cast<unsigned char*>(s.ozws);
+  int* E = reinterpret_cast<int*>(base);
+  int* F = reinterpret_cast<int*>(base + L.f_off);
+  unsigned char* Ap = base + L.a_off;
+  unsigned char* Bp = base + L.b_off;
+  // op(A) row i, element k: A[i + k lda] (ta 0) or A[k + i lda]; op(B) column j, element k:
+  // B[k + j ldb] (tb 0) or B[j + k ldb].  Zero patterns: op(A)[i,k] = 0 for k > i (tri_a 1) or
+  // k < i (tri_a 2); op(B)[k,j] = 0 for k < j (tri_b 1) or k > j (tri_b 2).
+  const long long a_sr = q.ta ? q.lda : 1, a_sk = q.ta ? 1 : q.lda;
+  const long long b_sr = q.tb ? 1 : q.ldb, b_sk = q.tb ? q.ldb : 1;
+  const int keep_a = q.tri_a == 1 ? 1 : (q.tri_a == 2 ? 2 : 0);
+  const int keep_b = q.tri_b == 1 ? 2 : (q.tri_b == 2 ? 1 : 0);
+  const int MT = (int)(L.Mp / OM), NT = (int)(L.Np / ON);
+  for (int k0 = 0; k0 < std::max(q.K, 1); k0 += KMAX) {
+    const int Kc = std::max(0, std::min(KMAX, q.K - k0));
+    const int KT = (Kc + KS - 1) / KS;
+    if (Kc > 0) {
+      cudaMemsetAsync(E, 0x80, L.Mp * sizeof(int), s.stream);
+      cudaMemsetAsync(F, 0x80, L.Np * sizeof(int), s.stream);
+      const dim3 eb(32, 8);
+      GEV_COUNT(s);
+      k_vec_exp<<<dim3(a_sr == 1 ? cdiv(q.M, 32) : cdiv(q.M, 8), cdiv(Kc, 1024)), eb, 0, s.stream>>>(
+          q.M, Kc, k0, q.A + k0 * a_sk, a_sr, a_sk, keep_a, E);
+      GEV_COUNT(s);
+      k_vec_exp<<<dim3(b_sr == 1 ? cdiv(q.N, 32) : cdiv(q.N, 8), cdiv(Kc, 1024)), eb, 0, s.stream>>>(
+          q.N, Kc, k0, q.B + k0 * b_sk, b_sr, b_sk, keep_b, F);
+      GEV_COUNT(s);
+      k_split<<<cdiv((long long)MT * OM * 2 * KT, 256), 256, 0, s.stream>>>(q.M, Kc, k0, q.A + k0 * a_sk, a_sr,
+                                                                           a_sk, keep_a, E, OM, MT, KT, Ap);
+      GEV_COUNT(s);
+      k_split<<<cdiv((long long)NT * ON * 2 * KT, 256), 256, 0, s.stream>>>(q.N, Kc, k0, q.B + k0 * b_sk, b_sr,
+                                                                           b_sk, keep_b, F, ON, NT, KT, Bp);
+    }
+    OzP p{};
+    p.M = q.M; p.N = q.N; p.K = Kc; p.koff = k0; p.c_lower = q.c_lower;
+    p.tri_a = q.tri_a; p.tri_b = q.tri_b;
+    p.MT = MT; p.NT = NT; p.KT = KT;
+    p.alpha = q.alpha; p.beta = (k0 == 0) ? q.beta : 1.0;
+    p.C = q.C; p.ldc = q.ldc; p.Ap = Ap; p.Bp = Bp; p.E = E; p.F = F; p.status = s.status;
+    // split K when the output has too few tiles to fill the GPU and K is long
+    long long tiles = (long long)MT * NT;
+    if (q.c_lower) tiles = (tiles + MT) / 2;
+    int ks = 1;
+    if (tiles < s.sms && KT >= 2 * CHUNK) {
+      ks = (int)std::min<long long>((2LL * s.sms + tiles - 1) / tiles, KT / CHUNK);
+      ks = std::min(ks, 16);
+      while (ks > 1 && (size_t)ks * q.M * q.N * sizeof(double) > s.splitws_bytes) --ks;
+    }
+    p.ksplit = ks;
+    p.ws = ks > 1 ? static_cast<double*>(s.splitws) : nullptr;
+    GEV_COUNT(s);
+    ozaki_kernel<<<dim3(MT * NT, ks), NTH, SMEM_OZ, s.stream>>>(p);
+    if (ks > 1) {
+      const long long total = (long long)q.M * q.N;
+      unsigned blocks = cdiv(total, 256);
+      if (blocks > 8u * s.sms) blocks = 8u * s.sms;
+      GEV_COUNT(s);
+      k_oz_reduce<<<blocks, 256, 0, s.stream>>>(q.M, q.N, ks, q.c_lower, p.alpha, p.ws, p.beta, q.C, q.ldc);
+    }
+  }
 }
 
 }  // namespace gev
 
+extern "C" size_t gev_gemm_f64_scratch_bytes(int M, int N, int K) {
+  if (M < 0 || N < 0 || K < 0) return 0;
+  return ((gev::gemm_f64_emulated_scratch(M, N, K) + 255) & ~(size_t)255) + ((size_t)16 << 20);
+}
+
 extern "C" int gev_gemm_f64(int M, int N, int K, int ta, int tb, double alpha, const double* A, int lda,
                             const double* B, int ldb, double beta, double* C, int ldc, int engine, void* stream,
-                            int* status_dev, int* scratch_dev) {
+                            int* status_dev, void* scratch_dev, size_t scratch_bytes) {
   using namespace gev;
   if (M < 0) return -1;
   if (N < 0) return -2;
@@ -346,7 +604,7 @@ extern "C" int gev_gemm_f64(int M, int N, int K, int ta, int tb, double alpha, c
   if (ldc < std::max(1, M)) return -13;
   if (engine < 0 || engine > 1) return -14;
   if (!status_dev) return -16;
-  if (engine == 1 && !scratch_dev) return -17;
+  if (engine == 1 && (!scratch_dev || scratch_bytes < gev_gemm_f64_scratch_bytes(M, N, K))) return -17;
   Sys s;
   s.stream = (cudaStream_t)stream;
   int dev = 0, sms = 0;
@@ -354,10 +612,17 @@ extern "C" int gev_gemm_f64(int M, int N, int K, int ta, int tb, double alpha, c
   GEV_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   s.sms = sms > 0 ? sms : 152;
   s.status = status_dev;
-  s.ozws = scratch_dev;
   s.emu_fp64 = engine;
-  s.splitws = nullptr;
-  s.splitws_bytes = 0;
+  if (engine == 1) {  // planes first, then the split-K partials
+    const size_t planes = (gemm_f64_emulated_scratch(M, N, K) + 255) & ~(size_t)255;
+    s.ozws = scratch_dev;
+    s.ozws_bytes = planes;
+    s.splitws = static_cast<unsigned char*>(scratch_dev) + planes;
+    s.splitws_bytes = scratch_bytes - planes;
+  } else {
+    s.splitws = nullptr;
+    s.splitws_bytes = 0;
+  }
   gemm<double>(s, gp<double>(M, N, K, ta, tb, alpha, A, lda, B, ldb, beta, C, ldc));
   GEV_TRY(last_error());
   GEV_CUDA_TRY(cudaStreamSynchronize(s.stream));

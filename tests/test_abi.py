@@ -72,3 +72,16 @@ def test_oracle_is_not_imported_by_the_package():
         if f.endswith((".py", ".cu", ".cuh", ".h")):
             txt = open(f).read()
             assert "import oracle" not in txt and "oracle_gev" not in txt and "from oracle" not in txt, f
+
+
+def test_emulated_gemm_scratch_size_needs_no_gpu(L):
+    """The digit planes take 16 bytes per padded element of op(A) and op(B) (8 BF16 planes), with K
+    capped at one launch's 32768; negative sizes give 0."""
+    f = L.gev_gemm_f64_scratch_bytes
+    f.argtypes = [ctypes.c_int] * 3
+    f.restype = ctypes.c_size_t
+    assert f(-1, 5, 5) == 0
+    b = f(1000, 500, 3000)
+    assert b >= 16 * (1024 + 512) * 3008
+    assert f(1000, 500, 40000) == f(1000, 500, 32768)
+    assert f(10, 10, 0) > 0
