@@ -7,10 +7,11 @@ back-transforms, C = X^H Y) on inputs already resident in HBM.  H and S are 2 x 
 than L2 (129 MB), so no L2 flush is needed between steps.
 
 Printed (rank 0, one JSON line): seconds per solve (lower is better), the roofline entry of the
-dominant kernel (the FP64 DMMA GEMM: algorithmic flops of every launch / CUDA-event time of every
-launch, on the solve stream), the CPU oracle on a bounded sample, the end-to-end time through the
-Python API with pinned host buffers, the number of kernels launched, SM clocks sampled during the
-timed region.
+FP64 matrix products (algorithmic flops of every launch / CUDA-event time of every launch, on the
+solve stream; for products emulated on the BF16 tensor cores, 36 digit-pair products each against
+the BF16 peak), the plain FP64 form beside the mixed headline (native and emulated products), the
+CPU oracle on a bounded sample, the end-to-end time through the Python API with pinned host
+buffers, the number of kernels launched, SM clocks sampled during the timed region.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--n N --k K] [--impl reference]
 
@@ -34,6 +35,7 @@ sys.path.insert(0, ROOT)
 METRIC = "N=16384 gen. eigensolve s (FP64 vs mixed, resid≤1e-11); k-pt stream p50/p99 ms"
 FP64_NOMINAL_TF = 1.25      # GB300 FP64 (DMMA) nominal, dense
 BF16_NOMINAL_TF = 2250.0    # GB300 BF16 nominal, dense
+EMU_PAIRS = 36              # BF16 digit-pair products per emulated FP64 product (p + q <= 9, 8 planes)
 
 
 def peaks():
@@ -221,6 +223,9 @@ def main():
                     help="requests of the k-point serving stream reported beside (0 = none)")
     ap.add_argument("--stream-n-max", type=int, default=2048)
     ap.add_argument("--band-b", type=int, default=64)
+    ap.add_argument("--fp64-emulation", type=int, default=-1, choices=[-1, 0, 1],
+                    help="FP64 products of the headline solve: 1 = BF16 digit planes on the tensor "
+                         "cores, 0 = native DMMA, -1 = automatic (on for the mixed form)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -257,7 +262,7 @@ def main():
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream(dev)
     solver = gev.Solver(args.n, complex_=args.complex, device=dev, mixed=args.mixed,
-                        band_b=args.band_b, timing=2, stream=stream)
+                        band_b=args.band_b, timing=2, stream=stream, fp64_emulation=args.fp64_emulation)
     w = torch.empty(args.k, dtype=torch.float64, device=dev)
     Cb = torch.empty((args.k, args.n), dtype=solver.dtype, device=dev)
     for _ in range(args.warmup):
@@ -293,30 +298,51 @@ def main():
     gemm_fl = sum(r["gemm_flops"] for r in reps)
     gemm_calls = sum(r["gemm_calls"] for r in reps)
     mp, src = peaks()
-    fp64_peak = mp.get("bf16_tflops_sustained", 1764.7) * FP64_NOMINAL_TF / BF16_NOMINAL_TF
-    achieved = gemm_fl / (gemm_ms * 1e-3) / 1e12 if gemm_ms > 0 else None
+    emu_used = (not args.complex) and (args.fp64_emulation == 1 or (args.fp64_emulation == -1 and args.mixed))
+    fp64_tf = gemm_fl / (gemm_ms * 1e-3) / 1e12 if gemm_ms > 0 else None
+    if emu_used:
+        # each FP64 product runs as 36 BF16 digit-pair products on the tensor cores
+        peak = mp.get("bf16_tflops_sustained", 1764.7)
+        achieved = EMU_PAIRS * fp64_tf if fp64_tf else None
+        roof_kernel = ("ozaki_kernel + k_split/k_vec_exp (FP64 products as 36 BF16 digit-pair tcgen05 MMAs, "
+                       "achieved = 36 x FP64 algorithmic flops / time of every FP64 product launch)")
+        peak_source = f"{src} bf16_tflops_sustained"
+    else:
+        peak = mp.get("bf16_tflops_sustained", 1764.7) * FP64_NOMINAL_TF / BF16_NOMINAL_TF
+        achieved = fp64_tf
+        roof_kernel = "gemm_kernel<double> (FP64 DMMA mma.sync m8n8k4)"
+        peak_source = (f"{src} bf16 sustained x FP64/BF16 nominal ratio ({FP64_NOMINAL_TF}/{BF16_NOMINAL_TF})")
     step_ms = {k: statistics.median(r["ms"][k] for r in reps) for k in gev.STEP_NAMES}
     launches = int(statistics.median(r["launches"] for r in reps))
-    # the plain FP64 form on the same input, beside the mixed headline (1 warm-up, 1 timed solve)
-    plain = None
+    # the plain FP64 form on the same input, beside the mixed headline (1 warm-up, 1 timed solve):
+    # with native FP64 products (DMMA) and with FP64 products emulated on the BF16 tensor cores
+    plain = plain_emu = None
     if args.mixed and not args.no_plain_beside:
         solver.close()
-        ps = gev.Solver(args.n, complex_=args.complex, device=dev, mixed=False, band_b=args.band_b,
-                        timing=1, stream=stream)
-        ps.solve_cm(Hb, Sb, args.k, w, Cb)
-        torch.cuda.synchronize()
-        f0 = torch.cuda.Event(enable_timing=True)
-        f1 = torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        ps.solve_cm(Hb, Sb, args.k, w, Cb)
-        f1.record(stream)
-        torch.cuda.synchronize()
-        plain = {"value": f0.elapsed_time(f1) / 1e3, "unit": "s", "steps": 1, "warmup": 1,
-                 "steps_ms": ps.last_report["ms"],
-                 "max_abs_eig_err_vs_construction": float(np.max(np.abs(w.cpu().numpy() - p.lam[: args.k])))}
-        ps.close()
+
+        def time_plain(emu):
+            ps = gev.Solver(args.n, complex_=args.complex, device=dev, mixed=False, band_b=args.band_b,
+                            timing=1, stream=stream, fp64_emulation=emu)
+            ps.solve_cm(Hb, Sb, args.k, w, Cb)
+            torch.cuda.synchronize()
+            f0 = torch.cuda.Event(enable_timing=True)
+            f1 = torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            ps.solve_cm(Hb, Sb, args.k, w, Cb)
+            f1.record(stream)
+            torch.cuda.synchronize()
+            out = {"value": f0.elapsed_time(f1) / 1e3, "unit": "s", "steps": 1, "warmup": 1,
+                   "fp64_products": "emulated (BF16 digit planes, tcgen05)" if emu else "native (DMMA)",
+                   "steps_ms": ps.last_report["ms"],
+                   "max_abs_eig_err_vs_construction": float(np.max(np.abs(w.cpu().numpy() - p.lam[: args.k])))}
+            ps.close()
+            return out
+
+        plain = time_plain(0)
+        if not args.complex:
+            plain_emu = time_plain(1)
         solver = gev.Solver(args.n, complex_=args.complex, device=dev, mixed=args.mixed,
-                            band_b=args.band_b, timing=0, stream=stream)
+                            band_b=args.band_b, timing=0, stream=stream, fp64_emulation=args.fp64_emulation)
     # end-to-end through the Python API with pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -356,15 +382,15 @@ def main():
         "max_abs_eig_err_vs_construction": err,
         "steps_ms": step_ms,
         "fp64_plain": plain,
+        "fp64_plain_emulated_products": plain_emu,
         "refine": {"iterations": reps[-1]["refine_iters"], "residual": reps[-1]["refine_resid"]}
         if args.mixed else None,
         "stream": stream_stats,
-        "roofline": {"bound": "tensor", "kernel": "gemm_kernel<double> (FP64 DMMA mma.sync m8n8k4)",
-                     "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                     "frac": (achieved / fp64_peak) if achieved else None, "traffic": None,
-                     "launches_timed": gemm_calls,
-                     "peak_source": f"{src} bf16 sustained x FP64/BF16 nominal ratio "
-                                    f"({FP64_NOMINAL_TF}/{BF16_NOMINAL_TF})"},
+        "roofline": {"bound": "tensor", "kernel": roof_kernel,
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "launches_timed": gemm_calls, "fp64_equivalent_tflops": fp64_tf,
+                     "peak_source": peak_source},
         "cpu_baseline": cb, "e2e": e2e, "gpu_launches": launches * args.steps, "clocks": clk,
     }
     print(json.dumps(line), flush=True)

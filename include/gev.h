@@ -81,8 +81,10 @@ typedef struct {
   int timing;            /* 1: record per-step times into gev_report.ms; 2: also time every GEMM
                             launch (CUDA events) and sum its algorithmic flops (gemm_ms/gemm_flops) */
   int fp64_emulation;    /* FP64 matrix products (real data): 1 = formed exactly from BF16 digit
-                            planes on the tensor cores (error below 2^-52 of the row/column scale),
+                            planes on the tensor cores (error below 2^-50 of the row/column scale),
                             0 = native FP64 DMMA, -1 = automatic (on for GEV_MIXED, off for GEV_PLAIN) */
+  int refine_rr_only;    /* mixed form: 1 = a Rayleigh-Ritz solve in every refinement iteration;
+                            0 = Ogita-Aishima steps once the basis is close (default) */
 } gev_opts;
 
 typedef struct {
@@ -97,6 +99,8 @@ typedef struct {
   int gemm_calls;           /* timing == 2: GEMM launches timed */
   double gemm_ms;           /* timing == 2: summed GEMM durations (ms, CUDA events) */
   double gemm_flops;        /* timing == 2: summed algorithmic GEMM flops (triangles excluded) */
+  int refine_oa_steps;      /* mixed form: iterations that took an Ogita-Aishima step in span(Y)
+                               instead of the Rayleigh-Ritz solve */
 } gev_report;
 
 /* Fill *opts with the defaults (device 0, default stream, GEV_PLAIN, automatic sizes). */

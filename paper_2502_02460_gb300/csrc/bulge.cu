@@ -20,6 +20,8 @@
 // (rows b+1 .. 2b-1 below the diagonal hold the bulge).
 #include <climits>
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "coop.cuh"
 
@@ -302,6 +304,83 @@ __global__ void __launch_bounds__(COLS) k_bt_bulge_level(int n, int k, int b, in
   }
 }
 
+// FP32 form of the level kernel: the same (group, task) blocks and level order, but each thread
+// applies the reflectors to its column from registers.  The 64 reflectors of a block are taken in
+// chunks of 8 (descending): a chunk touches window rows [q0, q0 + B + 7), which are moved from the
+// staged shared-memory window into registers, updated by the 8 reflectors (dot products with four
+// partial sums) and written back.  Reflector entries are shared-memory broadcasts, zero-padded
+// beyond the matrix end, so every chunk runs the same straight-line code.
+constexpr int BTF_COLS = 128, BTF_CH = 8;
+template <int B>
+__global__ void __launch_bounds__(BTF_COLS) k_bt_level_f32(int n, int k, int L, int ngroups, const float* V2,
+                                                           const float* tau2, int ntask, float* Y, long long ldy) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int g = max(0, ngroups - 1 - L) + blockIdx.x;
+  const int t = L - (ngroups - 1 - g);
+  if (g >= ngroups || t < 0 || t >= ntask) return;
+  const int s0 = g * B;
+  const int s1 = min(s0 + B - 1, n - 3);
+  const int w0 = s0 + 1 + t * B;
+  if (w0 >= n) return;
+  const int rows = min(n, s1 + 1 + t * B + B) - w0;  // <= 2B - 1
+  constexpr int LDZ = BTF_COLS + 1;
+  float* Zs = reinterpret_cast<float*>(smraw);          // 2B x LDZ
+  float* Vs = Zs + 2 * B * LDZ;                          // B x B (16-byte aligned rows)
+  float* ts = Vs + B * B;                                // B
+  const int c0 = blockIdx.y * BTF_COLS;
+  const int ncols = min(BTF_COLS, k - c0);
+  for (int idx = threadIdx.x; idx < B * B; idx += BTF_COLS) {
+    const int q = idx / B, i = idx % B;
+    const int p = s0 + q + 1 + t * B;
+    float v = 0.f;
+    if (s0 + q <= s1 && i < n - p) v = V2[((long long)(s0 + q) * ntask + t) * B + i];
+    Vs[idx] = v;
+  }
+  for (int q = threadIdx.x; q < B; q += BTF_COLS) ts[q] = (s0 + q <= s1) ? tau2[(long long)(s0 + q) * ntask + t] : 0.f;
+  for (int idx = threadIdx.x; idx < 2 * B * BTF_COLS; idx += BTF_COLS) {
+    const int r = idx % (2 * B), c = idx / (2 * B);  // consecutive threads: consecutive rows
+    float v = 0.f;
+    if (r < rows && c < ncols) v = Y[(w0 + r) + (long long)(c0 + c) * ldy];
+    Zs[r * LDZ + c] = v;
+  }
+  __syncthreads();
+  const int c = threadIdx.x;
+  for (int q0 = B - BTF_CH; q0 >= 0; q0 -= BTF_CH) {
+    float z[B + BTF_CH - 1];
+#pragma unroll
+    for (int j = 0; j < B + BTF_CH - 1; ++j) z[j] = Zs[(q0 + j) * LDZ + c];
+#pragma unroll
+    for (int u = BTF_CH - 1; u >= 0; --u) {
+      const float4* v4 = reinterpret_cast<const float4*>(Vs + (q0 + u) * B);
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll
+      for (int i = 0; i < B / 4; ++i) {
+        const float4 v = v4[i];
+        a0 = fmaf(v.x, z[u + 4 * i], a0);
+        a1 = fmaf(v.y, z[u + 4 * i + 1], a1);
+        a2 = fmaf(v.z, z[u + 4 * i + 2], a2);
+        a3 = fmaf(v.w, z[u + 4 * i + 3], a3);
+      }
+      const float w = ts[q0 + u] * ((a0 + a1) + (a2 + a3));
+#pragma unroll
+      for (int i = 0; i < B / 4; ++i) {
+        const float4 v = v4[i];
+        z[u + 4 * i] = fmaf(-v.x, w, z[u + 4 * i]);
+        z[u + 4 * i + 1] = fmaf(-v.y, w, z[u + 4 * i + 1]);
+        z[u + 4 * i + 2] = fmaf(-v.z, w, z[u + 4 * i + 2]);
+        z[u + 4 * i + 3] = fmaf(-v.w, w, z[u + 4 * i + 3]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < B + BTF_CH - 1; ++j) Zs[(q0 + j) * LDZ + c] = z[j];
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < 2 * B * BTF_COLS; idx += BTF_COLS) {
+    const int r = idx % (2 * B), cc = idx / (2 * B);
+    if (r < rows && cc < ncols) Y[(w0 + r) + (long long)(c0 + cc) * ldy] = Zs[r * LDZ + cc];
+  }
+}
+
 template <class T> size_t bulge_smem(int b) { return sizeof(T) * ((size_t)3 * b * (b + 1) + 2 * b) + 64; }
 
 }  // namespace
@@ -347,6 +426,25 @@ template <class T> int hb2st(Sys& s, double* d, double* e) {
 
 template <class T, int COLS> int bt_levels(Sys& s, int n, int k, int b, T* Y, int ldy);
 
+template <int B> int bt_levels_f32(Sys& s, int n, int k, float* Y, int ldy) {
+  const int ngroups = (n - 3) / B + 1;
+  const size_t smem = sizeof(float) * ((size_t)2 * B * (BTF_COLS + 1) + (size_t)B * B + B) + 64;
+  static bool attr = false;
+  if (!attr) {
+    GEV_TRY(allow_max_dyn_smem(k_bt_level_f32<B>));
+    attr = true;
+  }
+  const int nlevels = ngroups + s.ntask;
+  const unsigned ycb = cdiv(k, BTF_COLS);
+  for (int L = 0; L < nlevels; ++L) {
+    const int gmin = ngroups - 1 - L > 0 ? ngroups - 1 - L : 0;
+    GEV_COUNT(s);
+    k_bt_level_f32<B><<<dim3(ngroups - gmin, ycb), BTF_COLS, smem, s.stream>>>(
+        n, k, L, ngroups, (const float*)s.V2, (const float*)s.tau2, s.ntask, Y, ldy);
+  }
+  return last_error();
+}
+
 // Y (n x k) = Q2 D Z for real Z.
 template <class T> int bt_hb2st(Sys& s, const double* Z, int ldz, int k, T* Y, int ldy) {
   const int n = s.n, b = s.band_b_used;
@@ -359,6 +457,11 @@ template <class T> int bt_hb2st(Sys& s, const double* Z, int ldz, int k, T* Y, i
     GEV_TRY(last_error());
   }
   if (n <= 2) return 0;
+  if constexpr (std::is_same<T, float>::value) {
+    if (b == 16) return bt_levels_f32<16>(s, n, k, Y, ldy);
+    if (b == 32) return bt_levels_f32<32>(s, n, k, Y, ldy);
+    if (b == 64) return bt_levels_f32<64>(s, n, k, Y, ldy);
+  }
   // level-parallel application (see k_bt_bulge_level); one thread per column, as many columns
   // per block as the staged window (2b rows) allows in shared memory
   const size_t per_col = sizeof(T) * 2 * (size_t)b;

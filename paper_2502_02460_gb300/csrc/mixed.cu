@@ -8,7 +8,10 @@
 // problem (A, Y) in the spirit of Ogita-Aishima, with an FP64 Rayleigh-Ritz step in span(Y):
 //
 //   AY = A Y,  T = Y^T AY,  G = Y^T Y
-//   Rayleigh-Ritz: T W = G W Lambda (k x k pencil, solved by this library in FP64; W^T G W = I)
+//   Rayleigh-Ritz: T W = G W Lambda (k x k pencil, solved by this library in FP64; W^T G W = I);
+//     from the second iteration on, one Ogita-Aishima step W = I + E (first-order eigenvector and
+//     orthogonality corrections from T and G) replaces it whenever max |e_ij| <= 1e-2; a run that
+//     ends on such a step finishes with a first-order Loewdin orthonormalisation
 //   Y <- Y W,  AY <- AY W,  r_j = AY_j - lambda_j Y_j
 //   stop when ||r_j||_1 <= tol ||A||_1 ||y_j||_1 for every j, else
 //   out of span: W' = V^T r (V: the other n-k FP32 eigenvectors, mu their FP32 eigenvalues),
@@ -106,6 +109,64 @@ __global__ void k_scale_w(int m, int k, float* W, long long ldw, const double* l
   }
 }
 
+// One Ogita-Aishima step in span(Y) (their Algorithm 1 on the Gram data T = Y^T A Y,
+// G = Y^T Y, both taken symmetric): lambda_i = T_ii / G_ii and W = I + E with
+//   e_ii = (1 - G_ii) / 2,
+//   e_ij = (T_ij - lambda_j G_ij) / (lambda_j - lambda_i)   if |lambda_j - lambda_i| > delta,
+//   e_ij = -G_ij / 2                                          otherwise.
+// *emax receives max |e_ij| (bit pattern of a non-negative double, atomicMax).
+__global__ void k_oa_step(int k, const double* T, const double* G, double delta, double* W, double* lam,
+                          unsigned long long* emax) {
+  const long long total = (long long)k * k;
+  double m = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % k), j = (int)(t / k);
+    const double li = T[i + (long long)i * k] / G[i + (long long)i * k];
+    double e;
+    if (i == j) {
+      e = 0.5 * (1.0 - G[t]);
+      W[t] = 1.0 + e;
+      lam[i] = li;
+    } else {
+      // symmetric parts: the rounding asymmetry of the products, divided by small gaps, would
+      // otherwise break e_ij + e_ji = -G_ij (first-order orthogonality)
+      const long long tt = j + (long long)i * k;
+      const double tij = 0.5 * (T[t] + T[tt]), gij = 0.5 * (G[t] + G[tt]);
+      const double lj = T[j + (long long)j * k] / G[j + (long long)j * k];
+      const double gap = lj - li;
+      e = (fabs(gap) > delta) ? (tij - lj * gij) / gap : -0.5 * gij;
+      W[t] = e;
+    }
+    m = fmax(m, fabs(e));
+  }
+  m = wmax(m);
+  if ((threadIdx.x & 31) == 0) atomicMax(emax, (unsigned long long)__double_as_longlong(m));
+}
+
+// First-order Loewdin orthonormalisation from G = Y^T Y: W = I + (I - G_sym) / 2, so that
+// (Y W)^T (Y W) = I + O((G - I)^2).  One block per column j; *dmax receives the largest column
+// 1-norm of G - I (bit pattern of a non-negative double, atomicMax).
+__global__ void k_lowdin(int k, const double* G, double* W, unsigned long long* dmax) {
+  const int j = blockIdx.x;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    const double g = 0.5 * (G[i + (long long)j * k] + G[j + (long long)i * k]);
+    const double d = (i == j ? 1.0 : 0.0) - g;
+    W[i + (long long)j * k] = (i == j ? 1.0 : 0.0) + 0.5 * d;
+    s += fabs(d);
+  }
+  __shared__ double red[32];
+  s = wsum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    atomicMax(dmax, (unsigned long long)__double_as_longlong(t));
+  }
+}
+
 }  // namespace
 
 int solve_mixed(Sys& s, const double* H, int ldh, const double* S, int lds, int k, double* evals, double* C,
@@ -169,7 +230,7 @@ int solve_mixed(Sys& s, const double* H, int ldh, const double* S, int lds, int 
   double* lam = s.e;                     // k (the tridiagonal is consumed)
   double* rn = s.d;                      // k (after the column sums of A)
   double* yn = (double*)s.phase;         // k
-  double* scal = (double*)s.small;       // [0] ||A||_1, [1] max ||r_j||_1, [2] max ||y_j||_1
+  double* scal = (double*)s.small;       // [0] ||A||_1, [1] max ||r_j||_1, [2] max ||y_j||_1, [3] max |e_ij|
   float* Rf = Y32 + (size_t)n * n;       // n x k, second half of the FP32 eigenvector buffer
   float* Wp = (float*)s.V2;              // (n-k) x k
   const float* Vp = Y32 + (size_t)k * n;
@@ -201,17 +262,37 @@ int solve_mixed(Sys& s, const double* H, int ldh, const double* S, int lds, int 
     s.sub = h;
     s.sub_n = k;
   }
-  int it = 0;
+  int it = 0, oa_steps = 0;
   double resid = 0.0;
   bool converged = false;
+  // largest first-order coefficient for which an Ogita-Aishima step is taken instead of the
+  // Rayleigh-Ritz solve (its neglected second-order terms are then ~1e-4 and contract
+  // quadratically in the following steps)
+  constexpr double kOaMaxCorrection = 1e-2;
   for (;; ++it) {
     gemm(s, gp<double>(n, k, n, 0, 0, 1.0, A, n, Yd, n, 0.0, AY, n));   // AY = A Y
     gemm(s, gp<double>(k, k, n, 1, 0, 1.0, Yd, n, AY, n, 0.0, T, k));   // T = Y^T A Y
     gemm(s, gp<double>(k, k, n, 1, 0, 1.0, Yd, n, Yd, n, 0.0, G, k));   // G = Y^T Y
-    gev_report sr;
-    const int rc = gev_solve((gev_sys*)s.sub, T, k, G, k, k, lam, W, k, &sr);
-    if (rc) return rc;
-    s.launches += sr.launches;
+    // after the first iteration the basis is close to the eigenvectors: one Ogita-Aishima step in
+    // span(Y) replaces the Rayleigh-Ritz solve while its corrections stay small
+    bool oa = false;
+    double emax = 0.0;
+    if (it > 0 && !s.opts.refine_rr_only) {
+      GEV_CUDA_TRY(cudaMemsetAsync(scal + 3, 0, sizeof(double), st));
+      GEV_COUNT(s);
+      k_oa_step<<<std::min<unsigned>(cdiv((long long)k * k, 256), 16u * s.sms), 256, 0, st>>>(
+          k, T, G, 1e-12 * anorm, W, lam, (unsigned long long*)(scal + 3));
+      GEV_CUDA_TRY(cudaMemcpyAsync(&emax, scal + 3, sizeof(double), cudaMemcpyDeviceToHost, st));
+      GEV_CUDA_TRY(cudaStreamSynchronize(st));
+      oa = emax <= kOaMaxCorrection;
+      if (oa) ++oa_steps;
+    }
+    if (!oa) {
+      gev_report sr;
+      const int rc = gev_solve((gev_sys*)s.sub, T, k, G, k, k, lam, W, k, &sr);
+      if (rc) return rc;
+      s.launches += sr.launches;
+    }
     gemm(s, gp<double>(n, k, k, 0, 0, 1.0, Yd, n, W, k, 0.0, Yn, n));   // Ritz vectors
     gemm(s, gp<double>(n, k, k, 0, 0, 1.0, AY, n, W, k, 0.0, AYn, n));  // A times them
     GEV_COUNT(s);
@@ -224,7 +305,25 @@ int solve_mixed(Sys& s, const double* H, int ldh, const double* S, int lds, int 
     GEV_CUDA_TRY(cudaStreamSynchronize(st));
     resid = hs[1] / (anorm * (hs[2] > 0 ? hs[2] : 1.0));
     std::swap(Yd, Yn);  // Yd = the Ritz vectors
-    if (resid <= tol) { converged = true; break; }
+    if (resid <= tol && !oa) { converged = true; break; }  // Rayleigh-Ritz vectors: orthonormal in FP64
+    if (resid <= tol) {
+      // an Ogita-Aishima step leaves second-order defects in orthogonality: finish with a
+      // first-order Loewdin step; it moves the residuals by at most ||A|| max_j sum_i |G - I|_ij
+      gemm(s, gp<double>(k, k, n, 1, 0, 1.0, Yd, n, Yd, n, 0.0, G, k));
+      GEV_CUDA_TRY(cudaMemsetAsync(scal + 3, 0, sizeof(double), st));
+      GEV_COUNT(s);
+      k_lowdin<<<k, 256, 0, st>>>(k, G, W, (unsigned long long*)(scal + 3));
+      double dmax = 0.0;
+      GEV_CUDA_TRY(cudaMemcpyAsync(&dmax, scal + 3, sizeof(double), cudaMemcpyDeviceToHost, st));
+      GEV_CUDA_TRY(cudaStreamSynchronize(st));
+      if (resid + dmax <= tol) {
+        gemm(s, gp<double>(n, k, k, 0, 0, 1.0, Yd, n, W, k, 0.0, Yn, n));
+        std::swap(Yd, Yn);
+        resid += dmax;
+        converged = true;
+        break;
+      }
+    }
     if (it >= maxit || n == k) break;
     GemmP<float> g = gp<float>(n - k, k, n, 1, 0, 1.0f, Vp, n, Rf, n, 0.0f, Wp, n - k);
     gemm32<float, float>(s, g, Wp, 1.0f, 0.0f);  // W' = V^T r
@@ -237,6 +336,7 @@ int solve_mixed(Sys& s, const double* H, int ldh, const double* S, int lds, int 
   if (rep) {
     rep->refine_iters = it + 1;
     rep->refine_resid = resid;
+    rep->refine_oa_steps = oa_steps;
   }
   // ---- FP64: C = X^T Y
   mark(GEV_STEP_MULT);

@@ -47,7 +47,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("prec", ctypes.c_int),
                 ("band_b", ctypes.c_int), ("panel_nb", ctypes.c_int), ("refine_tol", ctypes.c_double),
                 ("refine_max_iter", ctypes.c_int), ("workspace_limit", ctypes.c_size_t),
-                ("timing", ctypes.c_int), ("fp64_emulation", ctypes.c_int)]
+                ("timing", ctypes.c_int), ("fp64_emulation", ctypes.c_int),
+                ("refine_rr_only", ctypes.c_int)]
 
 
 class Report(ctypes.Structure):
@@ -55,14 +56,15 @@ class Report(ctypes.Structure):
                 ("reused_factor", ctypes.c_int), ("refine_resid", ctypes.c_double),
                 ("ms", ctypes.c_double * NSTEPS), ("workspace_bytes", ctypes.c_size_t),
                 ("launches", ctypes.c_longlong), ("gemm_calls", ctypes.c_int),
-                ("gemm_ms", ctypes.c_double), ("gemm_flops", ctypes.c_double)]
+                ("gemm_ms", ctypes.c_double), ("gemm_flops", ctypes.c_double),
+                ("refine_oa_steps", ctypes.c_int)]
 
     def as_dict(self):
         return {"info": self.info, "deflated": self.deflated, "refine_iters": self.refine_iters,
                 "reused_factor": self.reused_factor, "refine_resid": self.refine_resid,
                 "ms": dict(zip(STEP_NAMES, list(self.ms))), "workspace_bytes": self.workspace_bytes,
                 "launches": self.launches, "gemm_calls": self.gemm_calls, "gemm_ms": self.gemm_ms,
-                "gemm_flops": self.gemm_flops}
+                "gemm_flops": self.gemm_flops, "refine_oa_steps": self.refine_oa_steps}
 
 
 _lib = None
@@ -141,7 +143,7 @@ class Solver:
     def __init__(self, n: int, complex_: bool = False, device=None, mixed: bool = False,
                  band_b: int = 0, panel_nb: int = 0, timing: int = 0, stream=None,
                  workspace_limit: int = 0, refine_tol: float = 0.0, refine_max_iter: int = 0,
-                 fp64_emulation: int = -1):
+                 fp64_emulation: int = -1, refine_rr_only: int = 0):
         import torch
 
         if not torch.cuda.is_available():
@@ -165,6 +167,7 @@ class Solver:
         o.refine_tol = refine_tol
         o.refine_max_iter = refine_max_iter
         o.fp64_emulation = fp64_emulation
+        o.refine_rr_only = refine_rr_only
         self.opts = o
         h = ctypes.c_void_p()
         _check(lib().gev_setup(ctypes.byref(h), n, GEV_C128 if complex_ else GEV_F64, ctypes.byref(o)),

@@ -86,3 +86,18 @@ def test_mixed_complex_not_available(dev):
         with pytest.raises(gv().GevError) as ei:
             s.solve_cm(gv().cm_from_numpy(p.H, dev), gv().cm_from_numpy(p.S, dev), 5)
         assert ei.value.code == 7
+
+
+@pytest.mark.parametrize("n,k,cluster", [(1500, 400, False), (1200, 300, True)])
+def test_mixed_oa_steps_keep_the_bounds(dev, n, k, cluster):
+    """Larger cases reach the Ogita-Aishima regime after the first Rayleigh-Ritz step (the report
+    counts those steps); the result must keep the oracle bounds either way, also with a 1e-8 cluster
+    of 16 eigenvalues inside the wanted set."""
+    p = inputs.make_problem(n, k, seed=700 + n, cluster=cluster)
+    w, C, rep = mixed_solve(p, k, dev)
+    assert 0 <= rep["refine_oa_steps"] <= rep["refine_iters"] - 1
+    h1 = norm1(p.H)
+    assert np.max(np.abs(w - p.lam[:k])) <= 1e-11 * h1
+    r, o = oracle.check(p.H, p.S, w, C)
+    assert r <= 1e-11, r
+    assert o <= 1e-12 * np.sqrt(n), o
