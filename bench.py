@@ -223,6 +223,9 @@ def main():
                     help="requests of the k-point serving stream reported beside (0 = none)")
     ap.add_argument("--stream-n-max", type=int, default=2048)
     ap.add_argument("--band-b", type=int, default=64)
+    ap.add_argument("--fp32-products", type=int, default=-1, choices=[-1, 0, 3, 6],
+                    help="mixed form, FP32 products: 6 / 3 = BF16x6 / BF16x3 on the tensor cores, "
+                         "0 = FP32 CUDA cores, -1 = automatic")
     ap.add_argument("--fp64-emulation", type=int, default=-1, choices=[-1, 0, 1],
                     help="FP64 products of the headline solve: 1 = BF16 digit planes on the tensor "
                          "cores, 0 = native DMMA, -1 = automatic (on for the mixed form)")
@@ -262,7 +265,8 @@ def main():
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream(dev)
     solver = gev.Solver(args.n, complex_=args.complex, device=dev, mixed=args.mixed,
-                        band_b=args.band_b, timing=2, stream=stream, fp64_emulation=args.fp64_emulation)
+                        band_b=args.band_b, timing=2, stream=stream, fp64_emulation=args.fp64_emulation,
+                        fp32_products=args.fp32_products)
     w = torch.empty(args.k, dtype=torch.float64, device=dev)
     Cb = torch.empty((args.k, args.n), dtype=solver.dtype, device=dev)
     for _ in range(args.warmup):
@@ -342,7 +346,8 @@ def main():
         if not args.complex:
             plain_emu = time_plain(1)
         solver = gev.Solver(args.n, complex_=args.complex, device=dev, mixed=args.mixed,
-                            band_b=args.band_b, timing=0, stream=stream, fp64_emulation=args.fp64_emulation)
+                            band_b=args.band_b, timing=0, stream=stream, fp64_emulation=args.fp64_emulation,
+                            fp32_products=args.fp32_products)
     # end-to-end through the Python API with pinned host buffers
     e2e = None
     if not args.no_e2e:

@@ -85,6 +85,9 @@ typedef struct {
                             0 = native FP64 DMMA, -1 = automatic (on for GEV_MIXED, off for GEV_PLAIN) */
   int refine_rr_only;    /* mixed form: 1 = a Rayleigh-Ritz solve in every refinement iteration;
                             0 = Ogita-Aishima steps once the basis is close (default) */
+  int fp32_products;     /* mixed form, FP32 matrix products: 6 = BF16x6 split products on the tensor
+                            cores (FP32-level accuracy), 3 = BF16x3 (about 16 bits), 0 = FP32 CUDA
+                            cores, -1 = automatic (6) */
 } gev_opts;
 
 typedef struct {

@@ -2,10 +2,9 @@
  * gev_kernels.h -- the matrix products of the mixed-precision form, as C entry points.
  *
  * The mixed form runs its reduction and back-transforms in FP32 (the single/double-precision pattern
- * named in the section "Future Plans and Challenges").  Its products are formed on the tensor cores
- * from BF16 splits: a = a_hi + a_lo with a_hi = bf16(a), a_lo = bf16(a - a_hi), and
- * a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi with FP32 accumulation (about 16 correct bits per
- * product); the result is then refined in FP64 by the solver.
+ * named in the section "Future Plans and Challenges").  Its large FP32 products are formed on the
+ * tensor cores from BF16 splits (gev_gemm_f32, engines 1 and 2); its FP64 products from exact BF16
+ * digit planes (gev_gemm_f64, engine 1).  The result is refined in FP64 by the solver.
  */
 #ifndef GEV_KERNELS_H
 #define GEV_KERNELS_H
@@ -17,15 +16,23 @@ extern "C" {
 #endif
 
 /* C = alpha op(A) op(B) + beta C, FP32, column-major device pointers on the current device.
-     ta, tb     : 0 = as stored, 1 = transposed
-     engine     : 1 = BF16x3 tensor-core products (tcgen05), 0 = FP32 CUDA-core FMAs
-     stream     : cudaStream_t (NULL = legacy default), synchronised before return
-     status_dev : device pointer to 16 ints the kernel may write (a bounded wait that expired writes
-                  a non-zero code to status_dev[1]); the caller zeroes and reads it
+     ta, tb        : 0 = as stored, 1 = transposed
+     engine        : 0 = FP32 CUDA-core FMAs; on the tensor cores (tcgen05), from the BF16 split
+                     x = x1 + x2 + x3 (exact for FP32 x): 1 = BF16x6, the 6 split products with
+                     p + q <= 4 (FP32-level accuracy), 2 = BF16x3, the products x1y1 + x1y2 + x2y1
+                     (about 16 significant bits); FP32 accumulation in tensor memory
+     stream        : cudaStream_t (NULL = legacy default), synchronised before return
+     status_dev    : device pointer to 16 ints the kernel may write (a bounded wait that expired writes
+                     a non-zero code to status_dev[1]); the caller zeroes and reads it
+     scratch_dev   : engines 1, 2: device scratch of scratch_bytes >= gev_gemm_f32_scratch_bytes(M, N, K)
+                     (split planes, about 6 (M + N) K bytes, plus split-K partials); ignored by engine 0
    Returns 0, -i for an invalid i-th argument, or GEV_ERR_CUDA.  Allocates nothing. */
 int gev_gemm_f32(int M, int N, int K, int ta, int tb, float alpha, const float* A, int lda,
                  const float* B, int ldb, float beta, float* C, int ldc, int engine, void* stream,
-                 int* status_dev);
+                 int* status_dev, void* scratch_dev, size_t scratch_bytes);
+
+/* Bytes of scratch gev_gemm_f32 needs for engines 1 and 2 (0 for negative sizes). */
+size_t gev_gemm_f32_scratch_bytes(int M, int N, int K);
 
 /* C = alpha op(A) op(B) + beta C in FP64 (real), column-major device pointers, current device.
      engine        : 0 = native FP64 tensor path (DMMA), 1 = emulated on the BF16 tensor cores: every

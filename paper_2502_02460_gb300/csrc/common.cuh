@@ -126,6 +126,10 @@ struct Sys;
 template <class T> void gemm(Sys& s, GemmP<T> p);
 // FP32 SIMT GEMM (gemm32.cu): inputs TI (float or double, converted on load), output TO.
 template <class TI, class TO> void gemm32(Sys& s, const GemmP<TI>& p, TO* C, float alpha, float beta);
+// FP32 GEMM from BF16 split products on tcgen05 (tc_gemm.cu); false when s.ozws is too small
+template <class TI, class TO>
+bool gemm_tc32(Sys& s, const GemmP<TI>& q, TO* C, float alpha, float beta, int nprod);
+size_t gemm_tc32_scratch(int M, int N, int K);  // bytes of s.ozws for an M x N x K product
 template <> void gemm<float>(Sys& s, GemmP<float> p);  // FP32: gemm32<float, float>
 void gemm_account(Sys& s, int* calls, double* ms, double* flops);
 void gemm_f64_emulated(Sys& s, const GemmP<double>& p);
@@ -184,6 +188,7 @@ struct Sys {
   double* R3 = nullptr;
   void* sub = nullptr;    // mixed form: handle of the k x k Rayleigh-Ritz pencil (gev_sys*)
   int emu_fp64 = 0;       // 1: real FP64 GEMMs formed on the tensor cores (ozaki.cu)
+  int fp32_tc = 0;        // FP32 GEMMs: 6 / 3 = BF16x6 / BF16x3 tensor products when large (tc_gemm.cu), 0 = CUDA cores
   void* ozws = nullptr;   // emulated FP64 GEMM: exponents + digit planes (gemm_f64_emulated_scratch)
   size_t ozws_bytes = 0;
   int sub_n = 0;

@@ -160,6 +160,10 @@ __global__ void splitk_reduce32(G32<TI, TO> p) {
 
 template <class TI, class TO> void gemm32(Sys& s, const GemmP<TI>& q, TO* C, float alpha, float beta) {
   if (q.M <= 0 || q.N <= 0) return;
+  // large products go to the tensor cores (BF16 split products, tc_gemm.cu) when enabled
+  if (s.fp32_tc && q.M >= 128 && q.N >= 128 && q.K >= 32 && (double)q.M * q.N * q.K >= 1.0e8 &&
+      gemm_tc32<TI, TO>(s, q, C, alpha, beta, s.fp32_tc))
+    return;
   G32<TI, TO> p{};
   p.M = q.M; p.N = q.N; p.K = q.K; p.ta = q.ta; p.tb = q.tb; p.tri_a = q.tri_a; p.tri_b = q.tri_b;
   p.c_lower = q.c_lower; p.alpha = alpha; p.beta = beta; p.A = q.A; p.lda = q.lda; p.B = q.B;

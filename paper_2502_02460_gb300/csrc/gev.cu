@@ -62,7 +62,8 @@ size_t carve(Sys& s, char* base) {
   size_t panel = (size_t)4096 * (2 * b + 8) * es * 2;
   size_t opanel = L.add(panel);
   size_t ost = L.add(sizeof(int) * ST_COUNT);
-  const size_t ozb = s.emu_fp64 ? gemm_f64_emulated_scratch((int)n, (int)n, (int)n) : 0;
+  size_t ozb = s.emu_fp64 ? gemm_f64_emulated_scratch((int)n, (int)n, (int)n) : 0;
+  if (s.fp32_tc) ozb = std::max(ozb, gemm_tc32_scratch((int)n, (int)n, (int)n));
   size_t ooz = L.add(ozb);
   const bool mixed = s.opts.prec == GEV_MIXED;
   size_t oR1 = L.add(mixed ? n * n * 8 : 8), oR2 = L.add(mixed ? n * n * 8 : 8), oR3 = L.add(mixed ? n * n * 8 : 8);
@@ -101,6 +102,7 @@ void fill_defaults(gev_opts* o) {
   o->workspace_limit = 0;
   o->timing = 0;
   o->fp64_emulation = -1;
+  o->fp32_products = -1;
 }
 
 int init_sys(Sys& s, int n, int dtype, const gev_opts* opts) {
@@ -115,6 +117,11 @@ int init_sys(Sys& s, int n, int dtype, const gev_opts* opts) {
   s.b = pick_band(n, s.opts.band_b);
   s.emu_fp64 = s.opts.fp64_emulation < 0 ? (s.opts.prec == GEV_MIXED ? 1 : 0) : (s.opts.fp64_emulation ? 1 : 0);
   if (dtype == GEV_C128) s.emu_fp64 = 0;
+  s.fp32_tc = 0;
+  if (s.opts.prec == GEV_MIXED) {
+    const int f = s.opts.fp32_products;
+    s.fp32_tc = (f < 0 || f == 6) ? 6 : (f == 3 ? 3 : 0);
+  }
   return 0;
 }
 

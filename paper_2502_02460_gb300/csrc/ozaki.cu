@@ -428,25 +428,39 @@ __global__ void __launch_bounds__(NTH, 1) ozaki_kernel(OzP p) {
       }
       if (gi < p.M) {
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const int gj = n0 + col0 + cb + q;
-          if (gj >= p.N || (p.c_lower && gi < gj)) continue;
-          double v = 0.0;
-          if (any) {
-            const int Fj = p.F[gj];
-            if (Ei >= EXP_BAD || Fj >= EXP_BAD) {
-              v = __longlong_as_double(0x7FF8000000000000ll);  // an Inf / NaN entry reached this output
-            } else if (Ei >= -1100 && Fj >= -1100) {
-              const double sum = (double)acc[cb + q] * 0x1p-49 + (double)__uint_as_float(r[q]);
-              v = scale2(sum, Ei + Fj + 2);
-            }
+        for (int h = 0; h < 16; h += 8) {
+          // the loads of 8 outputs (column exponents, C) first, so that they overlap
+          const bool read_c = p.ksplit == 1 && p.beta != 0.0;
+          double cin[8];
+          int fj[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int gj = n0 + col0 + cb + h + u;
+            const bool ok = gj < p.N && !(p.c_lower && gi < gj);
+            fj[u] = (ok && any) ? p.F[gj] : EXP_ZERO;
+            cin[u] = (ok && read_c) ? p.C[gi + gj * p.ldc] : 0.0;
           }
-          if (p.ksplit > 1) {
-            p.ws[(long long)blockIdx.y * p.M * p.N + gi + (long long)gj * p.M] = v;
-          } else {
-            double* cp = &p.C[gi + gj * p.ldc];
-            const double o = p.alpha * v;
-            *cp = (p.beta != 0.0) ? o + p.beta * (*cp) : o;
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int q = h + u;
+            const int gj = n0 + col0 + cb + q;
+            if (gj >= p.N || (p.c_lower && gi < gj)) continue;
+            double v = 0.0;
+            if (any) {
+              const int Fj = fj[u];
+              if (Ei >= EXP_BAD || Fj >= EXP_BAD) {
+                v = __longlong_as_double(0x7FF8000000000000ll);  // an Inf / NaN entry reached this output
+              } else if (Ei >= -1100 && Fj >= -1100) {
+                const double sum = (double)acc[cb + q] * 0x1p-49 + (double)__uint_as_float(r[q]);
+                v = scale2(sum, Ei + Fj + 2);
+              }
+            }
+            if (p.ksplit > 1) {
+              p.ws[(long long)blockIdx.y * p.M * p.N + gi + (long long)gj * p.M] = v;
+            } else {
+              const double o = p.alpha * v;
+              p.C[gi + gj * p.ldc] = read_c ? o + p.beta * cin[u] : o;
+            }
           }
         }
       }

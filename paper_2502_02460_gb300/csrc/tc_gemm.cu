@@ -1,284 +1,355 @@
-// FP32 GEMM from BF16x3 products on the 5th-generation tensor cores (tcgen05, kind::f16, FP32
-// accumulation in tensor memory), for the FP32 stages of the mixed form.
+// FP32 matrix products from BF16 split products on the 5th-generation tensor cores (tcgen05,
+// kind::f16, FP32 accumulation in tensor memory), for the FP32 stages of the mixed form.
 //
-//   a = a_hi + a_lo,  b = b_hi + b_lo  (a_hi = bf16(a), a_lo = bf16(a - a_hi))
-//   a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi          (three MMAs into one accumulator)
+//   x = x1 + x2 + x3 with x1 = bf16(x), x2 = bf16(x - x1), x3 = bf16(x - x1 - x2)  (each step exact
+//   in FP32, so x1 + x2 + x3 carries 24 significant bits: the FP32 value itself)
+//   a b ~ sum over the pairs (p, q) with p + q <= 4 of a_p b_q:
+//     BF16x6: a1b1 + a1b2 + a2b1 + a1b3 + a2b2 + a3b1  (dropped terms below 2^-24 |a b|: FP32 level)
+//     BF16x3: a1b1 + a1b2 + a2b1                        (about 16 significant bits)
+//   all products of one output accumulate in one FP32 tensor-memory accumulator.
 //
-// One CTA (128 threads) owns a 128 x 128 tile of C.  Producer: all threads load the FP32 (or FP64)
-// operand tiles with any transpose / triangular mask, split them into hi/lo BF16 and store them in
-// the canonical K-major, no-swizzle layout (core matrices of 8 rows x 16 bytes; LBO = 128 B between
-// core matrices along K, SBO = 1024 B along M/N).  One elected thread issues the MMAs of the 64-deep
-// slice (4 k-steps x 3 products) and commits them to an mbarrier; the next slice is staged into the
-// other buffer while they run.  Epilogue: the 4 warps read their 32 TMEM lanes (tcgen05.ld 32x32b)
-// and write C.  Every wait on the mbarrier is bounded; on expiry the kernel records ST_TIMEOUT,
-// waits (bounded) for its MMAs and frees its tensor memory before returning.
+// Data flow as in the emulated FP64 product (ozaki.cu): a split pass writes the three BF16 planes of
+// op(A) and op(B) to global memory in the order the MMAs consume them (one 16-deep k-slice of a
+// 128-row A tile = 3 planes x 4 KB; of a 256-column B tile = 3 x 8 KB), the GEMM kernel moves them
+// with bulk asynchronous copies into a 6-stage shared-memory ring, warp 9 issues the 128 x 256 x 16
+// MMAs, warps 0-7 read the accumulator (one TMEM lane per output row, half of the 256 columns each)
+// and write C.  Every mbarrier wait is bounded; on expiry the kernel records ST_TIMEOUT, waits
+// (bounded) for its copies and MMAs in flight, frees TMEM and returns.
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
+#include "tcgen05.cuh"
 
 namespace gev {
 
 namespace {
 
-constexpr int TM = 128, TN = 128, TK = 64, NTH = 128;
-constexpr int TMEM_COLS = 256;                      // >= TN (headroom keeps any N field in range)
-constexpr int OP_BYTES = TM * TK * 2;               // one BF16 operand tile: 16 KB
-constexpr int STAGE_BYTES = 4 * OP_BYTES;           // A_hi, A_lo, B_hi, B_lo
-constexpr int SMEM_BYTES = 2 * STAGE_BYTES + 1024;  // two stages + barriers
+using namespace tc;
 
-template <class TI, class TO> struct TcP {
-  int M, N, K, ta, tb, tri_a, tri_b, c_lower;
+constexpr int TM = 128, TN = 256, KS = 16, NSTAGE = 6, NPL = 3;
+constexpr int A_PL = TM * KS * 2;          // one plane of a 128 x 16 slice: 4 KB
+constexpr int B_PL = TN * KS * 2;          // one plane of a 256 x 16 slice: 8 KB
+constexpr int A_ST = NPL * A_PL;           // 12 KB
+constexpr int B_ST = NPL * B_PL;           // 24 KB
+constexpr int STAGE = A_ST + B_ST;         // 36 KB
+constexpr int SMEM_TC = NSTAGE * STAGE + 1024;
+constexpr int NEPI_W = 8;                  // epilogue warps: TMEM lanes 32 (w % 4), columns 128 (w / 4)
+constexpr int HC = TN / 2;
+constexpr int NTH = 32 * (NEPI_W + 2);     // + copy warp 8 + MMA warp 9
+constexpr int TMEM_COLS = 256;
+constexpr int GROUP_M = 8;
+
+// three BF16 planes of one operand (vector r, element k; rows padded to RT tiles of TR, k to KT
+// slices of 16).  One thread per (r, 8 consecutive k): 16 bytes to each plane.
+template <class TI>
+__global__ void k_split3(int R, int K, const TI* X, long long sr, long long sk, int keep, int TR, int RT, int KT,
+                         unsigned char* out) {
+  const long long Rp = (long long)RT * TR, G = 2LL * KT;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= Rp * G) return;
+  long long r, g;
+  if (sr == 1) { r = t % Rp; g = t / Rp; } else { g = t % G; r = t / G; }
+  uint32_t pk[NPL][4];
+#pragma unroll
+  for (int q = 0; q < 8; q += 2) {
+    uint16_t h[2][NPL];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const long long k = g * 8 + q + u;
+      float x = 0.f;
+      if (r < R && k < K && kept(keep, r, k)) x = (float)X[r * sr + k * sk];
+      const __nv_bfloat16 x1 = __float2bfloat16_rn(x);
+      const float r1 = x - __bfloat162float(x1);  // exact
+      const __nv_bfloat16 x2 = __float2bfloat16_rn(r1);
+      const float r2 = r1 - __bfloat162float(x2);  // exact
+      const __nv_bfloat16 x3 = __float2bfloat16_rn(r2);
+      h[u][0] = __bfloat16_as_ushort(x1);
+      h[u][1] = __bfloat16_as_ushort(x2);
+      h[u][2] = __bfloat16_as_ushort(x3);
+    }
+#pragma unroll
+    for (int p = 0; p < NPL; ++p) pk[p][q / 2] = (uint32_t)h[0][p] | ((uint32_t)h[1][p] << 16);
+  }
+  const long long rt = r / TR, kt = g >> 1;
+  const int plane_bytes = TR * KS * 2;
+  unsigned char* base =
+      out + ((rt * KT + kt) * NPL) * (long long)plane_bytes + toff16((int)(r % TR), (int)(g & 1) * 8);
+#pragma unroll
+  for (int p = 0; p < NPL; ++p)
+    *reinterpret_cast<uint4*>(base + (long long)p * plane_bytes) = make_uint4(pk[p][0], pk[p][1], pk[p][2], pk[p][3]);
+}
+
+struct TcP {
+  int M, N, K, c_lower, tri_a, tri_b;
+  int MT, NT, KT, ksplit, nprod, c_f64;
   float alpha, beta;
-  const TI* A;
-  long long lda;
-  const TI* B;
-  long long ldb;
-  TO* C;
+  void* C;
   long long ldc;
+  float* ws;  // split-K partials: ws[z M N + i + j M]
+  const unsigned char* Ap;
+  const unsigned char* Bp;
   int* status;
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-// offset (bytes) of element (r, k) of a 128 x 64 K-major tile in the no-swizzle canonical layout
-__device__ __forceinline__ int tile_off(int r, int k) {
-  return ((r >> 3) * (TK / 8) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2;
-}
-
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
-  const uint64_t lbo = 128, sbo = (TK / 8) * 128;
-  uint64_t d = 0;
-  d |= (uint64_t)((addr & 0x3FFFF) >> 4);
-  d |= (uint64_t)(lbo >> 4) << 16;
-  d |= (uint64_t)(sbo >> 4) << 32;
-  d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
-  // base offset 0, relative LBO mode, no swizzle (bits 61-63 = 0)
-  return d;
-}
-
-// kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16 (bits 7-9, 10-12 = 1), both K-major,
-// N >> 3 at bits 17-22, M >> 4 at bits 24-28.
-__host__ __device__ constexpr uint32_t instr_desc(int m, int n) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc, int acc) {
-  asm volatile(
-      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
-      "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t mbar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(mbar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// bounded wait for the given phase parity; false on expiry
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  for (long long it = 0; it < kSpinLimit; ++it) {
-    if (mbar_try_wait(mbar, parity)) return true;
-    __nanosleep(20);
-  }
-  return false;
-}
-
-template <class TI, class TO>
-__device__ __forceinline__ float load_a(const TcP<TI, TO>& p, int gi, int gk) {
-  if (gi >= p.M || gk >= p.K) return 0.f;
-  if ((p.tri_a == 1 && gk > gi) || (p.tri_a == 2 && gk < gi)) return 0.f;
-  return (float)((p.ta == 0) ? p.A[gi + gk * p.lda] : p.A[gk + gi * p.lda]);
-}
-template <class TI, class TO>
-__device__ __forceinline__ float load_b(const TcP<TI, TO>& p, int gk, int gj) {
-  if (gj >= p.N || gk >= p.K) return 0.f;
-  if ((p.tri_b == 1 && gk < gj) || (p.tri_b == 2 && gk > gj)) return 0.f;
-  return (float)((p.tb == 0) ? p.B[gk + gj * p.ldb] : p.B[gj + gk * p.ldb]);
-}
-
-__device__ __forceinline__ void split_store(unsigned char* hi, unsigned char* lo, int off, float v) {
-  const __nv_bfloat16 h = __float2bfloat16_rn(v);
-  const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
-  *reinterpret_cast<__nv_bfloat16*>(hi + off) = h;
-  *reinterpret_cast<__nv_bfloat16*>(lo + off) = l;
-}
-
-template <class TI, class TO>
-__global__ void __launch_bounds__(NTH, 1) tc_gemm_kernel(TcP<TI, TO> p) {
+__global__ void __launch_bounds__(NTH, 1) tc32_kernel(TcP p) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int m0 = blockIdx.x * TM, n0 = blockIdx.y * TN;
+  const int per_group = GROUP_M * p.NT;
+  const int first = (blockIdx.x / per_group) * GROUP_M;
+  const int gm = min(p.MT - first, GROUP_M);
+  const int within = blockIdx.x % per_group;
+  const int mt = first + within % gm, nt = within / gm;
+  const int m0 = mt * TM, n0 = nt * TN;
   if (p.c_lower && n0 > m0 + TM - 1) return;
-  int kb = 0, ke = p.K;
-  if (p.tri_a == 1) ke = min(ke, m0 + TM);
-  else if (p.tri_a == 2) kb = max(kb, m0);
-  if (p.tri_b == 1) kb = max(kb, n0);
-  else if (p.tri_b == 2) ke = min(ke, n0 + TN);
-  kb = kb / TK * TK;
-  unsigned char* stage0 = smem;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 2 * STAGE_BYTES);       // 2 barriers
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 2 * STAGE_BYTES + 64);
-  int* flag = reinterpret_cast<int*>(smem + 2 * STAGE_BYTES + 128);
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[0])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[1])));
-    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-    *flag = 0;
+  long long kb, ke;
+  tile_k_range(p.tri_a, p.tri_b, m0, TM, n0, TN, p.K, 0, kb, ke);
+  int s_lo = (int)(kb > 0 ? kb / KS : 0), s_hi = (int)(ke > 0 ? (ke + KS - 1) / KS : 0);
+  if (s_hi < s_lo) s_hi = s_lo;
+  if (p.ksplit > 1) {
+    const int tot = s_hi - s_lo, z = blockIdx.y;
+    const int a = s_lo + (int)((long long)tot * z / p.ksplit);
+    const int b = s_lo + (int)((long long)tot * (z + 1) / p.ksplit);
+    s_lo = a;
+    s_hi = b;
   }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
-                 "r"(TMEM_COLS));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-  const uint32_t tmem = *tmem_slot;
-  const uint32_t idesc = instr_desc(TM, TN);
+  const int nst = s_hi - s_lo;
 
-  const int nslices = (ke > kb) ? (ke - kb + TK - 1) / TK : 0;
-  uint32_t phase[2] = {0, 0};
-  int pending[2] = {0, 0};  // MMAs committed to barrier s and not yet waited for
-  bool ok = true;
-  for (int sl = 0; sl < nslices && ok; ++sl) {
-    const int s = sl & 1;
-    unsigned char* st = stage0 + s * STAGE_BYTES;
-    // the MMAs that last read this stage must be done before it is overwritten (thread 0 waits,
-    // the outcome is shared so every thread takes the same branch)
-    if (pending[s]) {
-      if (tid == 0) *flag = mbar_wait(smem_u32(&mbar[s]), phase[s]) ? 0 : 1;
-      __syncthreads();
-      const int expired = *flag;
-      __syncthreads();
-      if (expired) { ok = false; break; }
-      phase[s] ^= 1;
-      pending[s] = 0;
-    }
-    const int k0 = kb + sl * TK;
-    // producer: 128 x 64 tiles of op(A) and op(B)^T, split into hi / lo
-    for (int e = tid; e < TM * TK; e += NTH) {
-      int r, k;
-      if (p.ta == 0) { r = e % TM; k = e / TM; } else { k = e % TK; r = e / TK; }
-      int gk = k0 + k;
-      float v = (gk < ke) ? load_a(p, m0 + r, gk) : 0.f;
-      split_store(st, st + OP_BYTES, tile_off(r, k), v);
-      int c, kk;
-      if (p.tb == 0) { kk = e % TK; c = e / TK; } else { c = e % TN; kk = e / TN; }
-      gk = k0 + kk;
-      v = (gk < ke) ? load_b(p, gk, n0 + c) : 0.f;
-      split_store(st + 2 * OP_BYTES, st + 3 * OP_BYTES, tile_off(c, kk), v);
-    }
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      const uint32_t a_hi = smem_u32(st), a_lo = a_hi + OP_BYTES, b_hi = a_hi + 2 * OP_BYTES,
-                     b_lo = a_hi + 3 * OP_BYTES;
-#pragma unroll
-      for (int ks = 0; ks < TK / 16; ++ks) {
-        const uint32_t koff = ks * 2 * 128;  // 16 BF16 along K = two core matrices = 2 * LBO
-        const int first = (sl == 0 && ks == 0) ? 0 : 1;
-        mma_bf16(tmem, smem_desc(a_hi + koff), smem_desc(b_hi + koff), idesc, first);
-        mma_bf16(tmem, smem_desc(a_hi + koff), smem_desc(b_lo + koff), idesc, 1);
-        mma_bf16(tmem, smem_desc(a_lo + koff), smem_desc(b_hi + koff), idesc, 1);
-      }
-      mma_commit(smem_u32(&mbar[s]));
-    }
-    pending[s] = 1;
-  }
-  // drain: wait for every committed batch (bounded, thread 0)
+  unsigned char* ctrl = smem + NSTAGE * STAGE;
+  uint64_t* full = reinterpret_cast<uint64_t*>(ctrl);
+  uint64_t* empty = full + NSTAGE;
+  uint64_t* accd = empty + NSTAGE;  // accumulator complete
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(ctrl + 256);
+  volatile int* err = reinterpret_cast<volatile int*>(ctrl + 320);
+  int* issued = reinterpret_cast<int*>(ctrl + 384);
+  int* consumed = reinterpret_cast<int*>(ctrl + 448);
   if (tid == 0) {
-    bool good = ok;
-    for (int s = 0; s < 2; ++s)
-      if (pending[s] && !mbar_wait(smem_u32(&mbar[s]), phase[s])) good = false;
-    *flag = good ? 0 : 1;
-    if (!good) atomicCAS(&p.status[ST_TIMEOUT], 0, 401);
-  }
-  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-  __syncthreads();
-  const bool any_mma = nslices > 0 && *flag == 0;
-  // epilogue: warp w owns rows 32w .. 32w+31 (TMEM lanes), 16 columns per load
-  const int row = m0 + warp * 32 + lane;
-  for (int cb = 0; cb < TN; cb += 16) {
-    uint32_t r[16];
-    if (any_mma) {
-      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-    } else {
-#pragma unroll
-      for (int q = 0; q < 16; ++q) r[q] = 0u;
+    for (int s = 0; s < NSTAGE; ++s) {
+      mbar_init(su32(&full[s]), 1);
+      mbar_init(su32(&empty[s]), 1);
     }
-    if (row < p.M) {
+    mbar_init(su32(accd), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    *err = 0;
+    *issued = 0;
+    *consumed = 0;
+  }
+  if (warp == 0) tmem_alloc(su32(tslot), TMEM_COLS);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == NEPI_W) {
+    // ---- copy warp
+    if (lane == 0) {
+      const unsigned char* a_src = p.Ap + (long long)mt * p.KT * A_ST;
+      const unsigned char* b_src = p.Bp + (long long)nt * p.KT * B_ST;
+      for (int s = 0; s < nst; ++s) {
+        const int slot = s % NSTAGE;
+        if (s >= NSTAGE && !bar_wait(su32(&empty[slot]), ((s / NSTAGE) - 1) & 1, err)) {
+          if (!*err) *err = 421;
+          break;
+        }
+        const uint32_t fb = su32(&full[slot]);
+        mbar_expect_tx(fb, STAGE);
+        const uint32_t dst = su32(smem + slot * STAGE);
+        const long long kt = s_lo + s;
+        bulk_g2s(dst, a_src + kt * A_ST, A_ST, fb);
+        bulk_g2s(dst + A_ST, b_src + kt * B_ST, B_ST, fb);
+        *issued = s + 1;
+      }
+    }
+  } else if (warp == NEPI_W + 1) {
+    // ---- MMA warp: 6 (or 3) split products per 16-deep slice into one accumulator
+    if (lane == 0) {
+      const uint32_t id = idesc_bf16(TM, TN);
+      for (int s = 0; s < nst; ++s) {
+        const int slot = s % NSTAGE;
+        if (!bar_wait(su32(&full[slot]), (s / NSTAGE) & 1, err)) {
+          if (!*err) *err = 422;
+          break;
+        }
+        *consumed = s + 1;
+        fence_after();
+        const uint32_t a0 = su32(smem + slot * STAGE), b0 = a0 + A_ST;
+        // pairs in order of decreasing magnitude: (1,1) (1,2) (2,1) [(1,3) (2,2) (3,1)]
+        mma_bf16(tmem, sdesc16(a0), sdesc16(b0), id, s > 0 ? 1 : 0);
+        mma_bf16(tmem, sdesc16(a0), sdesc16(b0 + B_PL), id, 1);
+        mma_bf16(tmem, sdesc16(a0 + A_PL), sdesc16(b0), id, 1);
+        if (p.nprod == 6) {
+          mma_bf16(tmem, sdesc16(a0), sdesc16(b0 + 2 * B_PL), id, 1);
+          mma_bf16(tmem, sdesc16(a0 + A_PL), sdesc16(b0 + B_PL), id, 1);
+          mma_bf16(tmem, sdesc16(a0 + 2 * A_PL), sdesc16(b0), id, 1);
+        }
+        commit(su32(&empty[slot]));
+      }
+      commit(su32(accd));
+    }
+  } else {
+    // ---- epilogue warps
+    bool good = true;
+    if (nst > 0 && !bar_wait(su32(accd), 0, err)) {
+      good = false;
+      if (!*err) *err = 423;
+    }
+    const bool any = good && nst > 0;
+    fence_after();
+    const int quarter = warp & 3, col0 = (warp >> 2) * HC;
+    const int gi = m0 + quarter * 32 + lane;
+    const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)col0;
+    for (int cb = 0; cb < HC; cb += 16) {
+      uint32_t r[16];
+      if (any) {
+        tmem_ld16(lane_base + (uint32_t)cb, r);
+        tmem_wait_ld();
+      } else {
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const int col = n0 + cb + q;
-        if (col >= p.N || (p.c_lower && row < col)) continue;
-        TO* c = &p.C[row + (long long)col * p.ldc];
-        const TO out = (TO)(p.alpha * __uint_as_float(r[q]));
-        *c = (p.beta != 0.f) ? out + (TO)p.beta * (*c) : out;
+        for (int q = 0; q < 16; ++q) r[q] = 0u;
+      }
+      if (gi < p.M) {
+        const bool read_c = p.ksplit == 1 && p.beta != 0.f;
+#pragma unroll
+        for (int h = 0; h < 16; h += 8) {
+          // the loads of 8 outputs first, so that they overlap
+          double cin[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int gj = n0 + col0 + cb + h + u;
+            const bool ok = gj < p.N && !(p.c_lower && gi < gj);
+            cin[u] = 0.0;
+            if (ok && read_c)
+              cin[u] = p.c_f64 ? static_cast<const double*>(p.C)[gi + gj * p.ldc]
+                               : (double)static_cast<const float*>(p.C)[gi + gj * p.ldc];
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int gj = n0 + col0 + cb + h + u;
+            if (gj >= p.N || (p.c_lower && gi < gj)) continue;
+            const float v = __uint_as_float(r[h + u]);
+            if (p.ksplit > 1) {
+              p.ws[(long long)blockIdx.y * p.M * p.N + gi + (long long)gj * p.M] = v;
+            } else if (p.c_f64) {
+              const double o = (double)p.alpha * (double)v;
+              static_cast<double*>(p.C)[gi + gj * p.ldc] = read_c ? o + (double)p.beta * cin[u] : o;
+            } else {
+              const float o = p.alpha * v;
+              static_cast<float*>(p.C)[gi + gj * p.ldc] = read_c ? o + p.beta * (float)cin[u] : o;
+            }
+          }
+        }
       }
     }
   }
-  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
-  if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS));
+  if (tid == 0 && *err) {
+    // a wait gave up: let the copies already issued land before the shared memory is released
+    for (int s = *consumed; s < *issued; ++s) bar_wait_plain(su32(&full[s % NSTAGE]), (s / NSTAGE) & 1);
+    atomicCAS(&p.status[ST_TIMEOUT], 0, *err);
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
 }
+
+// C = alpha sum_z ws[z] + beta C in a fixed order (deterministic)
+template <class TO>
+__global__ void k_tc_reduce(int M, int N, int ks, int c_lower, float alpha, const float* ws, float beta, TO* C,
+                            long long ldc) {
+  const long long total = (long long)M * N;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % M), j = (int)(t / M);
+    if (c_lower && i < j) continue;
+    float s = 0.f;
+    for (int z = 0; z < ks; ++z) s += ws[(long long)z * total + t];
+    TO* c = &C[i + (long long)j * ldc];
+    const TO o = (TO)alpha * (TO)s;
+    *c = (beta != 0.f) ? o + (TO)beta * (*c) : o;
+  }
+}
+
+size_t rup(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 }  // namespace
 
-// C = alpha op(A) op(B) + beta C with BF16x3 tensor-core products (FP32 accumulation).  Falls back to
-// the FP32 SIMT GEMM (gemm32) when the output has too few tiles to fill the GPU (split K there).
-template <class TI, class TO> void gemm_bf16x3(Sys& s, const GemmP<TI>& q, TO* C, float alpha, float beta) {
-  if (q.M <= 0 || q.N <= 0) return;
-  const long long tiles = (long long)cdiv(q.M, TM) * cdiv(q.N, TN);
-  if (tiles * 2 < s.sms && q.K >= 512) {
-    gemm32<TI, TO>(s, q, C, alpha, beta);
-    return;
-  }
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute((const void*)tc_gemm_kernel<TI, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         SMEM_BYTES);
-    attr = true;
-  }
-  TcP<TI, TO> p{};
-  p.M = q.M; p.N = q.N; p.K = q.K; p.ta = q.ta; p.tb = q.tb; p.tri_a = q.tri_a; p.tri_b = q.tri_b;
-  p.c_lower = q.c_lower; p.alpha = alpha; p.beta = beta; p.A = q.A; p.lda = q.lda; p.B = q.B; p.ldb = q.ldb;
-  p.C = C; p.ldc = q.ldc; p.status = s.status;
-  dim3 grid(cdiv(q.M, TM), cdiv(q.N, TN));
-  GEV_COUNT(s);
-  tc_gemm_kernel<TI, TO><<<grid, NTH, SMEM_BYTES, s.stream>>>(p);
+size_t gemm_tc32_scratch(int M, int N, int K) {
+  const size_t Mp = rup(std::max(M, 1), TM), Np = rup(std::max(N, 1), TN), Kp = rup(std::max(K, 1), KS);
+  return rup(Mp * Kp * 2 * NPL, 256) + Np * Kp * 2 * NPL;
 }
 
-template void gemm_bf16x3<float, float>(Sys&, const GemmP<float>&, float*, float, float);
-template void gemm_bf16x3<float, double>(Sys&, const GemmP<float>&, double*, float, float);
-template void gemm_bf16x3<double, double>(Sys&, const GemmP<double>&, double*, float, float);
+// C = alpha op(A) op(B) + beta C with FP32 products formed from BF16 splits (nprod 6 or 3); the
+// split planes live in s.ozws (s.ozws_bytes >= gemm_tc32_scratch).  Returns false (nothing
+// launched) when the scratch is too small.
+template <class TI, class TO>
+bool gemm_tc32(Sys& s, const GemmP<TI>& q, TO* C, float alpha, float beta, int nprod) {
+  if (q.M <= 0 || q.N <= 0) return true;
+  if (!s.ozws || gemm_tc32_scratch(q.M, q.N, q.K) > s.ozws_bytes) return false;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute((const void*)tc32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_TC);
+    attr = true;
+  }
+  const size_t Mp = rup(q.M, TM), Kp = rup(std::max(q.K, 1), KS);
+  unsigned char* Ap = static_cast<unsigned char*>(s.ozws);
+  unsigned char* Bp = Ap + rup(Mp * Kp * 2 * NPL, 256);
+  const int MT = (int)(Mp / TM), NT = (int)(rup(q.N, TN) / TN), KT = (std::max(q.K, 0) + KS - 1) / KS;
+  // op(A) row i, element k: A[i + k lda] (ta 0) or A[k + i lda]; op(B) column j, element k:
+  // B[k + j ldb] (tb 0) or B[j + k ldb]
+  const long long a_sr = q.ta ? q.lda : 1, a_sk = q.ta ? 1 : q.lda;
+  const long long b_sr = q.tb ? 1 : q.ldb, b_sk = q.tb ? q.ldb : 1;
+  const int keep_a = q.tri_a == 1 ? 1 : (q.tri_a == 2 ? 2 : 0);
+  const int keep_b = q.tri_b == 1 ? 2 : (q.tri_b == 2 ? 1 : 0);
+  if (KT > 0) {
+    GEV_COUNT(s);
+    k_split3<TI><<<cdiv((long long)MT * TM * 2 * KT, 256), 256, 0, s.stream>>>(q.M, q.K, q.A, a_sr, a_sk, keep_a,
+                                                                              TM, MT, KT, Ap);
+    GEV_COUNT(s);
+    k_split3<TI><<<cdiv((long long)NT * TN * 2 * KT, 256), 256, 0, s.stream>>>(q.N, q.K, q.B, b_sr, b_sk, keep_b,
+                                                                              TN, NT, KT, Bp);
+  }
+  TcP p{};
+  p.M = q.M; p.N = q.N; p.K = std::max(q.K, 0); p.c_lower = q.c_lower; p.tri_a = q.tri_a; p.tri_b = q.tri_b;
+  p.MT = MT; p.NT = NT; p.KT = KT; p.nprod = nprod; p.c_f64 = std::is_same<TO, double>::value ? 1 : 0;
+  p.alpha = alpha; p.beta = beta; p.C = C; p.ldc = q.ldc; p.Ap = Ap; p.Bp = Bp; p.status = s.status;
+  long long tiles = (long long)MT * NT;
+  if (q.c_lower) tiles = (tiles + MT) / 2;
+  int ks = 1;
+  if (tiles < s.sms && KT >= 64) {
+    ks = (int)std::min<long long>((2LL * s.sms + tiles - 1) / tiles, KT / 32);
+    ks = std::min(ks, 16);
+    while (ks > 1 && (size_t)ks * q.M * q.N * sizeof(float) > s.splitws_bytes) --ks;
+  }
+  p.ksplit = ks;
+  p.ws = ks > 1 ? static_cast<float*>(s.splitws) : nullptr;
+  GEV_COUNT(s);
+  tc32_kernel<<<dim3(MT * NT, ks), NTH, SMEM_TC, s.stream>>>(p);
+  if (ks > 1) {
+    unsigned blocks = cdiv((long long)q.M * q.N, 256);
+    if (blocks > 8u * s.sms) blocks = 8u * s.sms;
+    GEV_COUNT(s);
+    k_tc_reduce<TO><<<blocks, 256, 0, s.stream>>>(q.M, q.N, ks, q.c_lower, alpha, p.ws, beta, C, q.ldc);
+  }
+  return true;
+}
+
+template bool gemm_tc32<float, float>(Sys&, const GemmP<float>&, float*, float, float, int);
+template bool gemm_tc32<float, double>(Sys&, const GemmP<float>&, double*, float, float, int);
+template bool gemm_tc32<double, double>(Sys&, const GemmP<double>&, double*, float, float, int);
+template bool gemm_tc32<double, float>(Sys&, const GemmP<double>&, float*, float, float, int);
 
 }  // namespace gev
 
+extern "C" size_t gev_gemm_f32_scratch_bytes(int M, int N, int K) {
+  if (M < 0 || N < 0 || K < 0) return 0;
+  return ((gev::gemm_tc32_scratch(M, N, K) + 255) & ~(size_t)255) + ((size_t)16 << 20);
+}
+
 extern "C" int gev_gemm_f32(int M, int N, int K, int ta, int tb, float alpha, const float* A, int lda,
                             const float* B, int ldb, float beta, float* C, int ldc, int engine, void* stream,
-                            int* status_dev) {
+                            int* status_dev, void* scratch_dev, size_t scratch_bytes) {
   using namespace gev;
   if (M < 0) return -1;
   if (N < 0) return -2;
@@ -291,8 +362,9 @@ extern "C" int gev_gemm_f32(int M, int N, int K, int ta, int tb, float alpha, co
   if (ldb < std::max(1, tb ? N : K)) return -10;
   if (!C && M > 0 && N > 0) return -12;
   if (ldc < std::max(1, M)) return -13;
-  if (engine < 0 || engine > 1) return -14;
+  if (engine < 0 || engine > 2) return -14;
   if (!status_dev) return -16;
+  if (engine > 0 && (!scratch_dev || scratch_bytes < gev_gemm_f32_scratch_bytes(M, N, K))) return -17;
   Sys s;
   s.stream = (cudaStream_t)stream;
   int dev = 0, sms = 0;
@@ -300,11 +372,20 @@ extern "C" int gev_gemm_f32(int M, int N, int K, int ta, int tb, float alpha, co
   GEV_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   s.sms = sms > 0 ? sms : 152;
   s.status = status_dev;
-  s.splitws = nullptr;
-  s.splitws_bytes = 0;
   GemmP<float> g = gp<float>(M, N, K, ta, tb, alpha, A, lda, B, ldb, beta, C, ldc);
-  if (engine == 1) gemm_bf16x3<float, float>(s, g, C, alpha, beta);
-  else gemm32<float, float>(s, g, C, alpha, beta);
+  if (engine == 0) {
+    s.splitws = nullptr;
+    s.splitws_bytes = 0;
+    gemm32<float, float>(s, g, C, alpha, beta);
+  } else {
+    const size_t planes = (gemm_tc32_scratch(M, N, K) + 255) & ~(size_t)255;
+    s.ozws = scratch_dev;
+    s.ozws_bytes = planes;
+    s.splitws = static_cast<unsigned char*>(scratch_dev) + planes;
+    s.splitws_bytes = scratch_bytes - planes;
+    s.fp32_tc = 0;  // gemm_tc32 directly, no size policy
+    if (!gemm_tc32<float, float>(s, g, C, alpha, beta, engine == 1 ? 6 : 3)) return GEV_ERR_CUDA;
+  }
   GEV_TRY(last_error());
   GEV_CUDA_TRY(cudaStreamSynchronize(s.stream));
   return 0;

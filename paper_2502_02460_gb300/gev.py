@@ -48,7 +48,7 @@ class Opts(ctypes.Structure):
                 ("band_b", ctypes.c_int), ("panel_nb", ctypes.c_int), ("refine_tol", ctypes.c_double),
                 ("refine_max_iter", ctypes.c_int), ("workspace_limit", ctypes.c_size_t),
                 ("timing", ctypes.c_int), ("fp64_emulation", ctypes.c_int),
-                ("refine_rr_only", ctypes.c_int)]
+                ("refine_rr_only", ctypes.c_int), ("fp32_products", ctypes.c_int)]
 
 
 class Report(ctypes.Structure):
@@ -143,7 +143,7 @@ class Solver:
     def __init__(self, n: int, complex_: bool = False, device=None, mixed: bool = False,
                  band_b: int = 0, panel_nb: int = 0, timing: int = 0, stream=None,
                  workspace_limit: int = 0, refine_tol: float = 0.0, refine_max_iter: int = 0,
-                 fp64_emulation: int = -1, refine_rr_only: int = 0):
+                 fp64_emulation: int = -1, refine_rr_only: int = 0, fp32_products: int = -1):
         import torch
 
         if not torch.cuda.is_available():
@@ -168,6 +168,7 @@ class Solver:
         o.refine_max_iter = refine_max_iter
         o.fp64_emulation = fp64_emulation
         o.refine_rr_only = refine_rr_only
+        o.fp32_products = fp32_products
         self.opts = o
         h = ctypes.c_void_p()
         _check(lib().gev_setup(ctypes.byref(h), n, GEV_C128 if complex_ else GEV_F64, ctypes.byref(o)),

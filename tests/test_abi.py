@@ -85,3 +85,13 @@ def test_emulated_gemm_scratch_size_needs_no_gpu(L):
     assert b >= 16 * (1024 + 512) * 3008
     assert f(1000, 500, 40000) == f(1000, 500, 32768)
     assert f(10, 10, 0) > 0
+
+
+def test_fp32_tensor_gemm_scratch_size_needs_no_gpu(L):
+    """Three BF16 planes (6 bytes) per padded element of op(A) (rows to 128) and op(B) (columns to 256)."""
+    f = L.gev_gemm_f32_scratch_bytes
+    f.argtypes = [ctypes.c_int] * 3
+    f.restype = ctypes.c_size_t
+    assert f(5, -1, 5) == 0
+    assert f(1000, 500, 3000) >= 6 * (1024 + 512) * 3008
+    assert f(0, 0, 0) > 0
