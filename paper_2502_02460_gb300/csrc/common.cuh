@@ -133,6 +133,7 @@ size_t gemm_tc32_scratch(int M, int N, int K);  // bytes of s.ozws for an M x N 
 template <> void gemm<float>(Sys& s, GemmP<float> p);  // FP32: gemm32<float, float>
 void gemm_account(Sys& s, int* calls, double* ms, double* flops);
 void gemm_f64_emulated(Sys& s, const GemmP<double>& p);
+void gemm_c128_emulated(Sys& s, const GemmP<zd>& p);  // real alpha, beta
 size_t gemm_f64_emulated_scratch(int M, int N, int K);  // bytes of s.ozws for an M x N x K product
 template <class T> GemmP<T> gp(int M, int N, int K, int ta, int tb, T alpha, const T* A, long long lda,
                                const T* B, long long ldb, T beta, T* C, long long ldc) {

@@ -258,15 +258,24 @@ template <class T> void gemm(Sys& s, GemmP<T> p) {
     s.gemm_fl[s.gemm_used] = algorithmic_flops(p);
     cudaEventRecord(ev0, s.stream);
   }
+  bool emulated = false;
   if constexpr (!is_cx<T>::value) {
     if (s.emu_fp64) {  // FP64 product from BF16 digit planes on the tensor cores
       gemm_f64_emulated(s, p);
-      if (s.account) {
-        cudaEventRecord(ev1, s.stream);
-        ++s.gemm_used;
-      }
-      return;
+      emulated = true;
     }
+  } else {
+    if (s.emu_fp64 && p.alpha.y == 0.0 && p.beta.y == 0.0) {  // through the real embedding
+      gemm_c128_emulated(s, p);
+      emulated = true;
+    }
+  }
+  if (emulated) {
+    if (s.account) {
+      cudaEventRecord(ev1, s.stream);
+      ++s.gemm_used;
+    }
+    return;
   }
   dim3 grid(cdiv(p.M, BM), cdiv(p.N, BN), 1);
   long long tiles = (long long)grid.x * grid.y;

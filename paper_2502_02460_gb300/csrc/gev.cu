@@ -62,7 +62,10 @@ size_t carve(Sys& s, char* base) {
   size_t panel = (size_t)4096 * (2 * b + 8) * es * 2;
   size_t opanel = L.add(panel);
   size_t ost = L.add(sizeof(int) * ST_COUNT);
-  size_t ozb = s.emu_fp64 ? gemm_f64_emulated_scratch((int)n, (int)n, (int)n) : 0;
+  size_t ozb = 0;
+  if (s.emu_fp64)  // complex products run in the real embedding: (2n x 2n) (2n x n)
+    ozb = s.dtype == GEV_C128 ? gemm_f64_emulated_scratch(2 * (int)n, (int)n, 2 * (int)n)
+                              : gemm_f64_emulated_scratch((int)n, (int)n, (int)n);
   if (s.fp32_tc) ozb = std::max(ozb, gemm_tc32_scratch((int)n, (int)n, (int)n));
   size_t ooz = L.add(ozb);
   const bool mixed = s.opts.prec == GEV_MIXED;
@@ -116,7 +119,6 @@ int init_sys(Sys& s, int n, int dtype, const gev_opts* opts) {
   if (s.opts.panel_nb > 0 && s.opts.panel_nb < 64) s.nb = (s.opts.panel_nb + 7) / 8 * 8;
   s.b = pick_band(n, s.opts.band_b);
   s.emu_fp64 = s.opts.fp64_emulation < 0 ? (s.opts.prec == GEV_MIXED ? 1 : 0) : (s.opts.fp64_emulation ? 1 : 0);
-  if (dtype == GEV_C128) s.emu_fp64 = 0;
   s.fp32_tc = 0;
   if (s.opts.prec == GEV_MIXED) {
     const int f = s.opts.fp32_products;

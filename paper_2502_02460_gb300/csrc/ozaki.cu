@@ -127,24 +127,52 @@ __device__ __forceinline__ bool kept(int keep, long long r, long long k) {
   return keep == 0 || (keep == 1 ? k <= r : k >= r);
 }
 
-// E[r] = max exponent over the kept entries of vector r: element k of vector r at X[r sr + k sk]
-// (absolute index k + koff for the mask; keep 1: k <= r, 2: k >= r).  E holds a very negative
-// value on entry (atomicMax).  Block 32 x 8; grid.y covers K in slices of 1024.
-__global__ void k_vec_exp(int R, int K, int koff, const double* X, long long sr, long long sk, int keep, int* E) {
+// One operand of a product as the exponent and split passes see it: vectors r (rows of op(A) or
+// columns of op(B)) of elements k.  Real data: element (r, k) at X[r sr + k sk].  Complex data
+// (double2 elements, strides in elements) enters through the real embedding of C = op(A) op(B):
+//   cx 1 (A side): vector r = 2i + a, element k = 2l + b of the 2 x 2 block [[x, -y], [y, x]] of
+//                  op(A)_il = x + iy;
+//   cx 2 (B side): vector j, element k = 2l + c: x (c = 0) or y (c = 1) of op(B)_lj = x + iy;
+// so that the real product of the two embedded operands is C with its real and imaginary parts in
+// rows 2i and 2i + 1.  conj negates y (conjugate transposes).  The zero pattern (keep 1: l <= i,
+// 2: l >= i; absolute l = local l + koff) refers to the complex indices.
+struct Opnd {
+  const void* X;
+  long long sr, sk;
+  int keep, cx, conj, koff;
+};
+
+__device__ __forceinline__ double opnd_at(const Opnd& o, long long r, long long k) {
+  if (o.cx == 0) {
+    if (!kept(o.keep, r, k + o.koff)) return 0.0;
+    return static_cast<const double*>(o.X)[r * o.sr + k * o.sk];
+  }
+  const long long ri = (o.cx == 1) ? (r >> 1) : r, ki = k >> 1;
+  if (!kept(o.keep, ri, ki + o.koff)) return 0.0;
+  const double2 z = static_cast<const double2*>(o.X)[ri * o.sr + ki * o.sk];
+  const double y = o.conj ? -z.y : z.y;
+  if (o.cx == 2) return (k & 1) ? y : z.x;
+  const long long a = r & 1, b = k & 1;
+  return (a == b) ? z.x : (a == 0 ? -y : y);
+}
+
+// E[r] = max exponent over the kept entries of vector r (R vectors of K elements).  E holds a very
+// negative value on entry (atomicMax).  Block 32 x 8; grid.y covers K in slices of 1024.
+// fast_r: consecutive vectors are adjacent in memory (threads run across vectors); otherwise a
+// warp reads along one vector.
+__global__ void k_vec_exp(int R, int K, Opnd o, int fast_r, int* E) {
   const int k_lo = blockIdx.y * 1024, k_hi = min(K, k_lo + 1024);
-  if (sr == 1) {  // the vectors run across the threads of a warp
+  if (fast_r) {
     const int r = blockIdx.x * 32 + threadIdx.x;
     if (r >= R) return;
     int e = EXP_ZERO;
-    for (int k = k_lo + threadIdx.y; k < k_hi; k += 8)
-      if (kept(keep, r, (long long)k + koff)) e = max(e, exp_above(X[r + (long long)k * sk]));
+    for (int k = k_lo + threadIdx.y; k < k_hi; k += 8) e = max(e, exp_above(opnd_at(o, r, k)));
     if (e != EXP_ZERO) atomicMax(&E[r], e);
-  } else {  // each vector is contiguous: a warp reads it
+  } else {
     const int r = blockIdx.x * 8 + threadIdx.y;
     if (r >= R) return;  // uniform across the warp
     int e = EXP_ZERO;
-    for (int k = k_lo + threadIdx.x; k < k_hi; k += 32)
-      if (kept(keep, r, (long long)k + koff)) e = max(e, exp_above(X[(long long)r * sr + k]));
+    for (int k = k_lo + threadIdx.x; k < k_hi; k += 32) e = max(e, exp_above(opnd_at(o, r, k)));
     e = __reduce_max_sync(0xffffffffu, e);
     if (threadIdx.x == 0 && e != EXP_ZERO) atomicMax(&E[r], e);
   }
@@ -182,20 +210,18 @@ __device__ __forceinline__ void digits(double x, int E, uint16_t out[NSLICE]) {
 // Digit planes of one operand: vector r (a row of op(A) or a column of op(B)), element k, rows
 // padded to RT tiles of TR, k to KT slices of 16.  One thread per (r, 8 consecutive k): it writes
 // 16 bytes to each of the 8 planes of tile (r / TR, k / 16).
-__global__ void k_split(int R, int K, int koff, const double* X, long long sr, long long sk, int keep,
-                        const int* E, int TR, int RT, int KT, unsigned char* out) {
+__global__ void k_split(int R, int K, Opnd o, int fast_r, const int* E, int TR, int RT, int KT, unsigned char* out) {
   const long long Rp = (long long)RT * TR, G = 2LL * KT;
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= Rp * G) return;
   long long r, g;
-  if (sr == 1) { r = t % Rp; g = t / Rp; } else { g = t % G; r = t / G; }
+  if (fast_r) { r = t % Rp; g = t / Rp; } else { g = t % G; r = t / G; }
   const int Er = (r < R) ? clamp_exp(E[r]) : EXP_ZERO;
   uint16_t dg[8][NSLICE];
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     const long long k = g * 8 + q;
-    double v = 0.0;
-    if (r < R && k < K && kept(keep, r, k + koff)) v = X[r * sr + k * sk];
+    const double v = (r < R && k < K) ? opnd_at(o, r, k) : 0.0;
     digits(v, Er, dg[q]);
   }
   const long long rt = r / TR, kt = g >> 1;
@@ -214,7 +240,7 @@ __global__ void k_split(int R, int K, int koff, const double* X, long long sr, l
 }
 
 struct OzP {
-  int M, N, K, koff, c_lower, tri_a, tri_b;
+  int M, N, K, koff, c_lower, tri_a, tri_b, cx;  // cx: complex product in the real embedding
   int MT, NT, KT, ksplit;
   double alpha, beta;
   double* C;
@@ -263,13 +289,18 @@ __global__ void __launch_bounds__(NTH, 1) ozaki_kernel(OzP p) {
   const int within = blockIdx.x % per_group;
   const int mt = first + within % gm, nt = within / gm;
   const int m0 = mt * OM, n0 = nt * ON;
-  if (p.c_lower && n0 > m0 + OM - 1) return;
+  // complex products: rows 2i, 2i + 1 and elements 2l, 2l + 1 belong to complex row i / element l
+  const int rs = p.cx ? 1 : 0;
+  const long long mr0 = m0 >> rs, mrn = OM >> rs;
+  if (p.c_lower && n0 > mr0 + mrn - 1) return;
   // k-slices holding non-zero products for this tile (absolute k = local k + koff)
-  long long kb = 0, ke = p.K;
-  if (p.tri_a == 1) ke = std::min<long long>(ke, (long long)m0 + OM - p.koff);
-  else if (p.tri_a == 2) kb = std::max<long long>(kb, (long long)m0 - p.koff);
+  long long kb = 0, ke = p.K >> rs;
+  if (p.tri_a == 1) ke = std::min<long long>(ke, mr0 + mrn - p.koff);
+  else if (p.tri_a == 2) kb = std::max<long long>(kb, mr0 - p.koff);
   if (p.tri_b == 1) kb = std::max<long long>(kb, (long long)n0 - p.koff);
   else if (p.tri_b == 2) ke = std::min<long long>(ke, (long long)n0 + ON - p.koff);
+  kb <<= rs;
+  ke <<= rs;
   int s_lo = (int)(kb / KS), s_hi = (int)(ke > 0 ? (ke + KS - 1) / KS : 0);
   if (s_hi < s_lo) s_hi = s_lo;
   if (p.ksplit > 1) {  // this CTA's share of the slices
@@ -436,7 +467,7 @@ __global__ void __launch_bounds__(NTH, 1) ozaki_kernel(OzP p) {
 #pragma unroll
           for (int u = 0; u < 8; ++u) {
             const int gj = n0 + col0 + cb + h + u;
-            const bool ok = gj < p.N && !(p.c_lower && gi < gj);
+            const bool ok = gj < p.N && !(p.c_lower && (gi >> rs) < gj);
             fj[u] = (ok && any) ? p.F[gj] : EXP_ZERO;
             cin[u] = (ok && read_c) ? p.C[gi + gj * p.ldc] : 0.0;
           }
@@ -444,7 +475,7 @@ __global__ void __launch_bounds__(NTH, 1) ozaki_kernel(OzP p) {
           for (int u = 0; u < 8; ++u) {
             const int q = h + u;
             const int gj = n0 + col0 + cb + q;
-            if (gj >= p.N || (p.c_lower && gi < gj)) continue;
+            if (gj >= p.N || (p.c_lower && (gi >> rs) < gj)) continue;
             double v = 0.0;
             if (any) {
               const int Fj = fj[u];
@@ -479,13 +510,14 @@ __global__ void __launch_bounds__(NTH, 1) ozaki_kernel(OzP p) {
 }
 
 // C = alpha sum_z ws[z] + beta C in a fixed order (deterministic)
-__global__ void k_oz_reduce(int M, int N, int ks, int c_lower, double alpha, const double* ws, double beta,
+// (rs = 1: complex product in the real embedding, rows 2i, 2i + 1 belong to complex row i)
+__global__ void k_oz_reduce(int M, int N, int ks, int c_lower, int rs, double alpha, const double* ws, double beta,
                             double* C, long long ldc) {
   const long long total = (long long)M * N;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(t % M), j = (int)(t / M);
-    if (c_lower && i < j) continue;
+    if (c_lower && (i >> rs) < j) continue;
     double s = 0.0;
     for (int z = 0; z < ks; ++z) s += ws[(long long)z * total + t];
     double* c = &C[i + (long long)j * ldc];
@@ -516,15 +548,20 @@ OzLayout oz_layout(int M, int N, int K) {
 
 size_t gemm_f64_emulated_scratch(int M, int N, int K) { return oz_layout(M, N, K).total; }
 
-// FP64 GEMM on the tensor cores (real data); scratch s.ozws of s.ozws_bytes >= gemm_f64_emulated_scratch.
-void gemm_f64_emulated(Sys& s, const GemmP<double>& q) {
-  if (q.M <= 0 || q.N <= 0) return;
+namespace {
+
+// C (M x N, real, ldc) = alpha op(A) op(B) + beta C with op(A) = the M x K operand a and op(B) the
+// N x K operand b (vectors = columns of op(B)), K in the operands' element units (embedded for
+// complex data); ka / kb: bytes of one underlying element step along K of a / b, to offset the
+// K pieces of one launch; rs = 1 for complex products.
+void emulate(Sys& s, int M, int N, int K, Opnd a, size_t a_kstep, Opnd b, size_t b_kstep, int tri_a, int tri_b,
+             int c_lower, int rs, double alpha, double beta, double* C, long long ldc) {
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute((const void*)ozaki_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_OZ);
     attr = true;
   }
-  const OzLayout L = oz_layout(q.M, q.N, q.K);
+  const OzLayout L = oz_layout(M, N, K);
   if (s.ozws == nullptr || L.total > s.ozws_bytes) {  // internal sizing error: fail the call loudly
     fprintf(stderr, "gev: emulated FP64 GEMM scratch too small (%zu < %zu bytes)\n", s.ozws_bytes, L.total);
     const int site = 499;
@@ -537,61 +574,86 @@ void gemm_f64_emulated(Sys& s, const GemmP<double>& q) {
   int* F = reinterpret_cast<int*>(base + L.f_off);
   unsigned char* Ap = base + L.a_off;
   unsigned char* Bp = base + L.b_off;
-  // op(A) row i, element k: A[i + k lda] (ta 0) or A[k + i lda]; op(B) column j, element k:
-  // B[k + j ldb] (tb 0) or B[j + k ldb].  Zero patterns: op(A)[i,k] = 0 for k > i (tri_a 1) or
-  // k < i (tri_a 2); op(B)[k,j] = 0 for k < j (tri_b 1) or k > j (tri_b 2).
-  const long long a_sr = q.ta ? q.lda : 1, a_sk = q.ta ? 1 : q.lda;
-  const long long b_sr = q.tb ? 1 : q.ldb, b_sk = q.tb ? q.ldb : 1;
-  const int keep_a = q.tri_a == 1 ? 1 : (q.tri_a == 2 ? 2 : 0);
-  const int keep_b = q.tri_b == 1 ? 2 : (q.tri_b == 2 ? 1 : 0);
+  const int fast_a = a.sr == 1, fast_b = b.sr == 1;
   const int MT = (int)(L.Mp / OM), NT = (int)(L.Np / ON);
-  for (int k0 = 0; k0 < std::max(q.K, 1); k0 += KMAX) {
-    const int Kc = std::max(0, std::min(KMAX, q.K - k0));
+  for (int k0 = 0; k0 < std::max(K, 1); k0 += KMAX) {  // K pieces (k0 even: whole complex elements)
+    const int Kc = std::max(0, std::min(KMAX, K - k0));
     const int KT = (Kc + KS - 1) / KS;
+    const int ku = k0 >> rs;  // the piece's first underlying element along K
+    Opnd ap = a, bp = b;
+    ap.X = static_cast<const unsigned char*>(a.X) + (size_t)ku * a_kstep;
+    bp.X = static_cast<const unsigned char*>(b.X) + (size_t)ku * b_kstep;
+    ap.koff = bp.koff = ku;
     if (Kc > 0) {
       cudaMemsetAsync(E, 0x80, L.Mp * sizeof(int), s.stream);
       cudaMemsetAsync(F, 0x80, L.Np * sizeof(int), s.stream);
       const dim3 eb(32, 8);
       GEV_COUNT(s);
-      k_vec_exp<<<dim3(a_sr == 1 ? cdiv(q.M, 32) : cdiv(q.M, 8), cdiv(Kc, 1024)), eb, 0, s.stream>>>(
-          q.M, Kc, k0, q.A + k0 * a_sk, a_sr, a_sk, keep_a, E);
+      k_vec_exp<<<dim3(fast_a ? cdiv(M, 32) : cdiv(M, 8), cdiv(Kc, 1024)), eb, 0, s.stream>>>(M, Kc, ap, fast_a, E);
       GEV_COUNT(s);
-      k_vec_exp<<<dim3(b_sr == 1 ? cdiv(q.N, 32) : cdiv(q.N, 8), cdiv(Kc, 1024)), eb, 0, s.stream>>>(
-          q.N, Kc, k0, q.B + k0 * b_sk, b_sr, b_sk, keep_b, F);
+      k_vec_exp<<<dim3(fast_b ? cdiv(N, 32) : cdiv(N, 8), cdiv(Kc, 1024)), eb, 0, s.stream>>>(N, Kc, bp, fast_b, F);
       GEV_COUNT(s);
-      k_split<<<cdiv((long long)MT * OM * 2 * KT, 256), 256, 0, s.stream>>>(q.M, Kc, k0, q.A + k0 * a_sk, a_sr,
-                                                                           a_sk, keep_a, E, OM, MT, KT, Ap);
+      k_split<<<cdiv((long long)MT * OM * 2 * KT, 256), 256, 0, s.stream>>>(M, Kc, ap, fast_a, E, OM, MT, KT, Ap);
       GEV_COUNT(s);
-      k_split<<<cdiv((long long)NT * ON * 2 * KT, 256), 256, 0, s.stream>>>(q.N, Kc, k0, q.B + k0 * b_sk, b_sr,
-                                                                           b_sk, keep_b, F, ON, NT, KT, Bp);
+      k_split<<<cdiv((long long)NT * ON * 2 * KT, 256), 256, 0, s.stream>>>(N, Kc, bp, fast_b, F, ON, NT, KT, Bp);
     }
     OzP p{};
-    p.M = q.M; p.N = q.N; p.K = Kc; p.koff = k0; p.c_lower = q.c_lower;
-    p.tri_a = q.tri_a; p.tri_b = q.tri_b;
+    p.M = M; p.N = N; p.K = Kc; p.koff = ku; p.c_lower = c_lower;
+    p.tri_a = tri_a; p.tri_b = tri_b; p.cx = rs;
     p.MT = MT; p.NT = NT; p.KT = KT;
-    p.alpha = q.alpha; p.beta = (k0 == 0) ? q.beta : 1.0;
-    p.C = q.C; p.ldc = q.ldc; p.Ap = Ap; p.Bp = Bp; p.E = E; p.F = F; p.status = s.status;
+    p.alpha = alpha; p.beta = (k0 == 0) ? beta : 1.0;
+    p.C = C; p.ldc = ldc; p.Ap = Ap; p.Bp = Bp; p.E = E; p.F = F; p.status = s.status;
     // split K when the output has too few tiles to fill the GPU and K is long
     long long tiles = (long long)MT * NT;
-    if (q.c_lower) tiles = (tiles + MT) / 2;
+    if (c_lower) tiles = (tiles + MT) / 2;
     int ks = 1;
     if (tiles < s.sms && KT >= 2 * CHUNK) {
       ks = (int)std::min<long long>((2LL * s.sms + tiles - 1) / tiles, KT / CHUNK);
       ks = std::min(ks, 16);
-      while (ks > 1 && (size_t)ks * q.M * q.N * sizeof(double) > s.splitws_bytes) --ks;
+      while (ks > 1 && (size_t)ks * M * N * sizeof(double) > s.splitws_bytes) --ks;
     }
     p.ksplit = ks;
     p.ws = ks > 1 ? static_cast<double*>(s.splitws) : nullptr;
     GEV_COUNT(s);
     ozaki_kernel<<<dim3(MT * NT, ks), NTH, SMEM_OZ, s.stream>>>(p);
     if (ks > 1) {
-      const long long total = (long long)q.M * q.N;
+      const long long total = (long long)M * N;
       unsigned blocks = cdiv(total, 256);
       if (blocks > 8u * s.sms) blocks = 8u * s.sms;
       GEV_COUNT(s);
-      k_oz_reduce<<<blocks, 256, 0, s.stream>>>(q.M, q.N, ks, q.c_lower, p.alpha, p.ws, p.beta, q.C, q.ldc);
+      k_oz_reduce<<<blocks, 256, 0, s.stream>>>(M, N, ks, c_lower, rs, p.alpha, p.ws, p.beta, C, ldc);
     }
   }
+}
+
+int keep_a_of(int tri_a) { return tri_a == 1 ? 1 : (tri_a == 2 ? 2 : 0); }
+int keep_b_of(int tri_b) { return tri_b == 1 ? 2 : (tri_b == 2 ? 1 : 0); }
+
+}  // namespace
+
+// FP64 GEMM on the tensor cores (real data); scratch s.ozws of s.ozws_bytes >= gemm_f64_emulated_scratch.
+// Zero patterns: op(A)[i,k] = 0 for k > i (tri_a 1) or k < i (tri_a 2); op(B)[k,j] = 0 for k < j
+// (tri_b 1) or k > j (tri_b 2).
+void gemm_f64_emulated(Sys& s, const GemmP<double>& q) {
+  if (q.M <= 0 || q.N <= 0) return;
+  // op(A) row i, element k: A[i + k lda] (ta 0) or A[k + i lda]; op(B) column j, element k:
+  // B[k + j ldb] (tb 0) or B[j + k ldb]
+  Opnd a{q.A, q.ta ? q.lda : 1, q.ta ? 1 : q.lda, keep_a_of(q.tri_a), 0, 0, 0};
+  Opnd b{q.B, q.tb ? 1 : q.ldb, q.tb ? q.ldb : 1, keep_b_of(q.tri_b), 0, 0, 0};
+  emulate(s, q.M, q.N, q.K, a, sizeof(double) * (size_t)a.sk, b, sizeof(double) * (size_t)b.sk, q.tri_a, q.tri_b,
+          q.c_lower, 0, q.alpha, q.beta, q.C, q.ldc);
+}
+
+// Complex FP64 GEMM on the tensor cores through the real embedding (2M x 2K) (2K x N): the
+// result's real and imaginary parts are rows 2i and 2i + 1 of the real view of C (leading
+// dimension 2 ldc).  alpha and beta must be real (the caller checks).  ta / tb 2: conjugate
+// transposes.
+void gemm_c128_emulated(Sys& s, const GemmP<zd>& q) {
+  if (q.M <= 0 || q.N <= 0) return;
+  Opnd a{q.A, q.ta ? q.lda : 1, q.ta ? 1 : q.lda, keep_a_of(q.tri_a), 1, q.ta == 2 ? 1 : 0, 0};
+  Opnd b{q.B, q.tb ? 1 : q.ldb, q.tb ? q.ldb : 1, keep_b_of(q.tri_b), 2, q.tb == 2 ? 1 : 0, 0};
+  emulate(s, 2 * q.M, q.N, 2 * q.K, a, sizeof(zd) * (size_t)a.sk, b, sizeof(zd) * (size_t)b.sk, q.tri_a, q.tri_b,
+          q.c_lower, 1, q.alpha.x, q.beta.x, reinterpret_cast<double*>(q.C), 2 * q.ldc);
 }
 
 }  // namespace gev

@@ -2,7 +2,8 @@
 
 Sizes span several 64-wide tiles and a ragged tail.  Bounds: the oracle and the GPU are two FP64
 routes to the same exact result, so entries agree to a small multiple of n * eps relative to the
-norm of the result (well-conditioned Toeplitz overlap, cond(S) ~ 10)."""
+norm of the result (well-conditioned Toeplitz overlap, cond(S) ~ 10).  The product-based steps run
+with native FP64 products (emu 0) and with products emulated on the BF16 tensor cores (emu 1)."""
 import numpy as np
 import pytest
 
@@ -43,14 +44,15 @@ def to_np(B):
     return gev.numpy_from_cm(B)
 
 
+@pytest.mark.parametrize("emu", [0, 1])
 @pytest.mark.parametrize("cx", [False, True])
 @pytest.mark.parametrize("n", SIZES)
-def test_potrf_matches_oracle(dev, cx, n):
+def test_potrf_matches_oracle(dev, cx, n, emu):
     p = inputs.make_problem(n, 1, seed=n, complex_=cx)
     S = inputs.lower_only(p.S, 7.0)  # upper triangle must not be read
     Lo, info = oracle.potrf(p.S)
     assert info == 0
-    with solver(n, cx, dev) as s:
+    with solver(n, cx, dev, fp64_emulation=emu) as s:
         B = to_dev(S, dev)
         assert s.potrf(B) == 0
         L = to_np(B)
@@ -68,12 +70,13 @@ def test_potrf_not_spd_reports_first_pivot(dev):
             assert s.potrf(B) == bad + 1
 
 
+@pytest.mark.parametrize("emu", [0, 1])
 @pytest.mark.parametrize("cx", [False, True])
 @pytest.mark.parametrize("n", SIZES)
-def test_trtri_inverts(dev, cx, n):
+def test_trtri_inverts(dev, cx, n, emu):
     p = inputs.make_problem(n, 1, seed=n + 1, complex_=cx)
     Lo, _ = oracle.potrf(p.S)
-    with solver(n, cx, dev) as s:
+    with solver(n, cx, dev, fp64_emulation=emu) as s:
         B = to_dev(Lo, dev)
         s.trtri(B)
         X = to_np(B)
@@ -82,30 +85,32 @@ def test_trtri_inverts(dev, cx, n):
     assert np.all(np.triu(X, 1) == 0)
 
 
+@pytest.mark.parametrize("emu", [0, 1])
 @pytest.mark.parametrize("cx", [False, True])
 @pytest.mark.parametrize("n", SIZES)
-def test_hegst_matches_oracle(dev, cx, n):
+def test_hegst_matches_oracle(dev, cx, n, emu):
     p = inputs.make_problem(n, 1, seed=n + 2, complex_=cx)
     Lo, _ = oracle.potrf(p.S)
     Ao, _ = oracle.reduce(p.H, Lo)
     X = np.linalg.inv(Lo)
     X = np.tril(X)
-    with solver(n, cx, dev) as s:
+    with solver(n, cx, dev, fp64_emulation=emu) as s:
         A = to_np(s.hegst(to_dev(inputs.lower_only(p.H, -5.0), dev), to_dev(X, dev)))
     assert np.max(np.abs(A - Ao)) <= 1e-12 * np.abs(Ao).max() * max(1, np.sqrt(n))
     assert np.array_equal(A, A.conj().T)
 
 
+@pytest.mark.parametrize("emu", [0, 1])
 @pytest.mark.parametrize("cx", [False, True])
 @pytest.mark.parametrize("n,k", [(1, 1), (65, 3), (200, 130), (333, 333)])
-def test_mult(dev, cx, n, k):
+def test_mult(dev, cx, n, k, emu):
     rng = np.random.default_rng(n + k)
     X = np.tril(rng.standard_normal((n, n)))
     Y = rng.standard_normal((n, k))
     if cx:
         X = X + 1j * np.tril(rng.standard_normal((n, n)))
         Y = Y + 1j * rng.standard_normal((n, k))
-    with solver(n, cx, dev) as s:
+    with solver(n, cx, dev, fp64_emulation=emu) as s:
         C = to_np(s.mult(to_dev(X, dev), to_dev(Y, dev), k))
     ref = X.conj().T @ Y
     assert np.max(np.abs(C - ref)) <= 1e-13 * n * np.abs(ref).max()
