@@ -228,7 +228,7 @@ def main():
                          "0 = FP32 CUDA cores, -1 = automatic")
     ap.add_argument("--fp64-emulation", type=int, default=-1, choices=[-1, 0, 1],
                     help="FP64 products of the headline solve: 1 = BF16 digit planes on the tensor "
-                         "cores, 0 = native DMMA, -1 = automatic (on for the mixed form)")
+                         "cores, 0 = native DMMA, -1 = automatic (1)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -302,7 +302,7 @@ def main():
     gemm_fl = sum(r["gemm_flops"] for r in reps)
     gemm_calls = sum(r["gemm_calls"] for r in reps)
     mp, src = peaks()
-    emu_used = (not args.complex) and (args.fp64_emulation == 1 or (args.fp64_emulation == -1 and args.mixed))
+    emu_used = args.fp64_emulation != 0
     fp64_tf = gemm_fl / (gemm_ms * 1e-3) / 1e12 if gemm_ms > 0 else None
     if emu_used:
         # each FP64 product runs as 36 BF16 digit-pair products on the tensor cores

@@ -80,9 +80,9 @@ typedef struct {
   size_t workspace_limit;/* bytes; 0 = no limit */
   int timing;            /* 1: record per-step times into gev_report.ms; 2: also time every GEMM
                             launch (CUDA events) and sum its algorithmic flops (gemm_ms/gemm_flops) */
-  int fp64_emulation;    /* FP64 matrix products (real data): 1 = formed exactly from BF16 digit
-                            planes on the tensor cores (error below 2^-50 of the row/column scale),
-                            0 = native FP64 DMMA, -1 = automatic (on for GEV_MIXED, off for GEV_PLAIN) */
+  int fp64_emulation;    /* FP64 matrix products: 1 = formed from exact BF16 digit planes on the tensor
+                            cores (error below about 2^-50 of the row/column scale; complex data
+                            through the real 2x2 embedding), 0 = native FP64 DMMA, -1 = automatic (1) */
   int refine_rr_only;    /* mixed form: 1 = a Rayleigh-Ritz solve in every refinement iteration;
                             0 = Ogita-Aishima steps once the basis is close (default) */
   int fp32_products;     /* mixed form, FP32 matrix products: 6 = BF16x6 split products on the tensor

@@ -118,7 +118,7 @@ int init_sys(Sys& s, int n, int dtype, const gev_opts* opts) {
   s.nb = 64;
   if (s.opts.panel_nb > 0 && s.opts.panel_nb < 64) s.nb = (s.opts.panel_nb + 7) / 8 * 8;
   s.b = pick_band(n, s.opts.band_b);
-  s.emu_fp64 = s.opts.fp64_emulation < 0 ? (s.opts.prec == GEV_MIXED ? 1 : 0) : (s.opts.fp64_emulation ? 1 : 0);
+  s.emu_fp64 = s.opts.fp64_emulation < 0 ? 1 : (s.opts.fp64_emulation ? 1 : 0);
   s.fp32_tc = 0;
   if (s.opts.prec == GEV_MIXED) {
     const int f = s.opts.fp32_products;

@@ -271,13 +271,13 @@ def test_repeated_solves_are_bitwise_identical(dev, cx):
 
 @pytest.mark.parametrize("cx", [False, True])
 @pytest.mark.parametrize("n,k,b", [(100, 33, 16), (333, 100, 32), (700, 210, 64), (1100, 300, 64)])
-def test_solve_with_emulated_fp64_products_matches_oracle(dev, cx, n, k, b):
-    """The FP64 solve with every matrix product formed on the BF16 tensor cores (digit planes,
-    fp64_emulation=1; complex products through the real embedding): same bounds as the native path.
-    Covers the triangular operand masks (inversion, Multiply step), conjugate transposes, lower-only
-    outputs and split K of the emulated products."""
+def test_solve_with_native_fp64_products_matches_oracle(dev, cx, n, k, b):
+    """The FP64 solve with every matrix product on the native FP64 tensor path (DMMA,
+    fp64_emulation=0; the other solve tests run the default, products emulated on the BF16 tensor
+    cores): same bounds.  Covers the triangular operand masks (inversion, Multiply step), conjugate
+    transposes, lower-only outputs and split K of both engines."""
     p = inputs.make_problem(n, k, seed=3000 + n, complex_=cx, cluster=(n == 700))
-    with gv().Solver(n, complex_=cx, device=dev, band_b=b, fp64_emulation=1) as s:
+    with gv().Solver(n, complex_=cx, device=dev, band_b=b, fp64_emulation=0) as s:
         w, Cb = s.solve_cm(gv().cm_from_numpy(p.H, dev), gv().cm_from_numpy(p.S, dev), k)
         w = w.cpu().numpy()
         C = gv().numpy_from_cm(Cb)
