@@ -37,6 +37,10 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 __device__ __forceinline__ zd warp_sum(zd v) { return make_zd(warp_sum(v.x), warp_sum(v.y)); }
+__device__ __forceinline__ float warp_sum(float v) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
 
 // Bounded acquire-wait until *flag >= target.  Thread 0 spins; returns false on timeout/abort.
 __device__ bool wait_ge(const int* flag, int target, int* status, int* abort_flag, int site) {
@@ -63,19 +67,44 @@ __device__ bool wait_ge(const int* flag, int target, int* status, int* abort_fla
   return ok != 0;
 }
 
+// Band -> tridiagonal by bulge chasing (one sweep per block at a time).  Task t of sweep s
+// annihilates the column below the band with one Householder reflector H = I - tau v v^H
+// (v_0 = 1) acting on rows p .. p+len-1, p = s + 1 + t b:
+//   L (the block left of the reflector's rows, the previous task's bulge) <- H L   (t > 0),
+//   D (the diagonal block)                                                  <- H D H^H,
+//   E (the block below D: the new bulge)                                    <- E H^H,
+// and the reflector is kept for back-transform 2.  Sweep s+1 may run task t once sweep s has
+// finished task t+2 (their blocks overlap up to there): a bounded wait on progress[s].
+// A task is a short dependent chain, and on GB300 the FP64 pipe executes a warp-wide FP64
+// instruction in ~19 cycles, so the FP64 form is bound by its count of FP64 instructions and the
+// FP32 form by latency.  Hence: all arithmetic in the data's own precision R (FP32 for the mixed
+// form); matrix-vector products with four threads per row / column (partial sums over every
+// fourth term, combined through shared memory: all eight warps, hence all four schedulers' FP64
+// pipes, take an equal share and no shuffle reductions are needed); element updates spread over
+// all threads; the
+// loads of the D and E blocks issued into registers right after the wait, so that their L2 latency
+// overlaps the reflector and the update of L.
 template <class T>
 __global__ void __launch_bounds__(NT) k_bulge(int n, int b, T* band, int ldb, T* V2, T* tau2, int ntask,
                                               int* progress, int* status, int* abort_flag) {
+  using R = typename std::conditional<std::is_same<T, float>::value, float, double>::type;
   extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr int PF = 64 * 64 / NT;  // register prefetch slots per thread (b <= 64)
   const int LD = b + 1;
   T* Ls = reinterpret_cast<T*>(smraw);
   T* Es = Ls + b * LD;
   T* Ds = Es + b * LD;
   T* v = Ds + b * LD;
   T* y = v + b;
+  T* w = y + b;
+  T* part4 = w + b;  // 4 x 64 partial sums of the matrix-vector products
   __shared__ T sh_tau, sh_beta, sh_scale;
-  __shared__ double sh_c;
+  __shared__ R sh_c;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int lb = __ffs(b) - 1;  // b is a power of two (16, 32, 64)
+  const int ci = tid & (b - 1), cj = tid >> lb, cstep = NT >> lb;
+  const int qi = tid & 63, qp = tid >> 6;  // matrix-vector products: row / column qi, quarter qp
+  static_assert(NT == 256, "the products use 4 x 64 threads");
 
   for (int s = blockIdx.x; s <= n - 3; s += gridDim.x) {
     bool pendingL = false;
@@ -89,23 +118,35 @@ __global__ void __launch_bounds__(NT) k_bulge(int n, int b, T* band, int ldb, T*
           for (int q = tid; q < b; q += NT) stcg_(&band[(b - q) + (long long)(pp + q) * ldb], Ls[q * LD]);
         break;
       }
-      // ---- generating vector x
+      const int p2 = p + len;
+      const int len2 = (p2 < n) ? min(b, n - p2) : 0;
+      // ---- prefetch D (lower triangle) and E into registers: thread (ci, cj) holds row ci,
+      // columns cj, cj + cstep, ... of each block
+      T dreg[PF], ereg[PF];
+#pragma unroll
+      for (int u = 0; u < PF; ++u) {
+        const int jj = cj + u * cstep;
+        dreg[u] = (jj < len && ci < len && ci >= jj) ? ldcg_(&band[(ci - jj) + (long long)(p + jj) * ldb])
+                                                     : zero_<T>();
+        ereg[u] = (jj < len && ci < len2) ? ldcg_(&band[(len + ci - jj) + (long long)(p + jj) * ldb]) : zero_<T>();
+      }
+      // ---- generating vector x and the reflector
       for (int i = tid; i < len; i += NT)
         v[i] = (t == 0) ? ldcg_(&band[(1 + i) + (long long)s * ldb]) : Ls[i];
       __syncthreads();
       if (warp == 0) {
-        double xn = 0.0;
-        for (int i = 1 + lane; i < len; i += 32) xn += abs2_(v[i]);
+        R xn = 0;
+        for (int i = 1 + lane; i < len; i += 32) xn += (R)abs2_(v[i]);
         xn = warp_sum(xn);
         if (lane == 0) {
           const T alpha = v[0];
-          if (xn == 0.0 && im_(alpha) == 0.0) {
+          if (xn == (R)0 && im_(alpha) == 0) {
             sh_tau = zero_<T>();
             sh_beta = alpha;
             sh_scale = zero_<T>();
           } else {
-            const double nrm = sqrt(abs2_(alpha) + xn);
-            const T bt = from_re<T>(re_(alpha) >= 0.0 ? -nrm : nrm);
+            const R nrm = sqrt((R)abs2_(alpha) + xn);
+            const T bt = from_re<T>(re_(alpha) >= 0 ? -nrm : nrm);
             sh_tau = div_(bt - alpha, bt);
             sh_beta = bt;
             sh_scale = div_(from_re<T>(1.0), alpha - bt);
@@ -121,74 +162,71 @@ __global__ void __launch_bounds__(NT) k_bulge(int n, int b, T* band, int ldb, T*
         for (int i = tid; i < len; i += NT)
           stcg_(&band[(1 + i) + (long long)s * ldb], i == 0 ? beta : zero_<T>());
       } else {
-        for (int i = tid; i < len; i += NT) Ls[i] = (i == 0) ? beta : zero_<T>();
-        const T ctau = conj_(tau);
-        for (int q = 1 + warp; q < b; q += NT / 32) {
+        if (qi >= 1 && qi < b) {  // w_q = conj(tau) v^H L(:, q): four partial sums per column
           T acc = zero_<T>();
-          for (int i = lane; i < len; i += 32) acc += cmul(v[i], Ls[i + q * LD]);
-          acc = ctau * warp_sum(acc);
-          for (int i = lane; i < len; i += 32) Ls[i + q * LD] -= v[i] * acc;
+          for (int i = qp; i < len; i += 4) acc += cmul(v[i], Ls[i + qi * LD]);
+          part4[qp * 64 + qi] = acc;
         }
         __syncthreads();
-        for (int idx = tid; idx < len * b; idx += NT) {
-          const int i = idx % len, q = idx / len;
-          stcg_(&band[(b + i - q) + (long long)(pp + q) * ldb], Ls[i + q * LD]);
+        if (tid >= 1 && tid < b)
+          w[tid] = conj_(tau) * ((part4[tid] + part4[64 + tid]) + (part4[128 + tid] + part4[192 + tid]));
+        __syncthreads();
+        if (ci < len) {
+          for (int q = (cj == 0 ? cstep : cj); q < b; q += cstep) Ls[ci + q * LD] -= v[ci] * w[q];
+          if (cj == 0) Ls[ci] = (ci == 0) ? beta : zero_<T>();
         }
+        __syncthreads();
+        if (ci < len)
+          for (int q = cj; q < b; q += cstep) stcg_(&band[(b + ci - q) + (long long)(pp + q) * ldb], Ls[ci + q * LD]);
       }
       // ---- (iii) two-sided update of the diagonal block
-      for (int idx = tid; idx < len * len; idx += NT) {
-        const int i = idx % len, j = idx / len;
-        if (i >= j) {
-          T val = ldcg_(&band[(i - j) + (long long)(p + j) * ldb]);
-          if (i == j) val = from_re<T>(re_(val));
-          Ds[i + j * LD] = val;
-          Ds[j + i * LD] = conj_(val);
+#pragma unroll
+      for (int u = 0; u < PF; ++u) {
+        const int jj = cj + u * cstep;
+        if (jj < len && ci < len && ci >= jj) {
+          T val = dreg[u];
+          if (ci == jj) val = from_re<T>(re_(val));
+          Ds[ci + jj * LD] = val;
+          Ds[jj + ci * LD] = conj_(val);
         }
+        if (jj < len && ci < len2) Es[ci + jj * LD] = ereg[u];
       }
       __syncthreads();
-      for (int i = tid; i < len; i += NT) {
+      if (qi < len) {  // y = D v: four partial sums per row
         T acc = zero_<T>();
-        for (int j = 0; j < len; ++j) acc += Ds[i + j * LD] * v[j];
-        y[i] = acc;
+        for (int j = qp; j < len; j += 4) acc += Ds[qi + j * LD] * v[j];
+        part4[qp * 64 + qi] = acc;
       }
+      __syncthreads();
+      if (tid < len) y[tid] = (part4[tid] + part4[64 + tid]) + (part4[128 + tid] + part4[192 + tid]);
       __syncthreads();
       if (warp == 0) {
         T acc = zero_<T>();
         for (int i = lane; i < len; i += 32) acc += cmul(v[i], y[i]);
         acc = warp_sum(acc);
-        if (lane == 0) sh_c = 0.5 * abs2_(tau) * re_(acc);
+        if (lane == 0) sh_c = (R)0.5 * (R)abs2_(tau) * (R)re_(acc);
       }
       __syncthreads();
-      for (int i = tid; i < len; i += NT) y[i] = tau * y[i] - sh_c * v[i];
+      for (int i = tid; i < len; i += NT) y[i] = tau * y[i] - from_re<T>(sh_c) * v[i];
       __syncthreads();
-      for (int idx = tid; idx < len * len; idx += NT) {
-        const int i = idx % len, j = idx / len;
-        if (i >= j) {
-          T val = Ds[i + j * LD] - (mulc(y[i], v[j]) + mulc(v[i], y[j]));
-          if (i == j) val = from_re<T>(re_(val));
-          stcg_(&band[(i - j) + (long long)(p + j) * ldb], val);
+      if (ci < len)
+        for (int jj = cj; jj <= ci; jj += cstep) {
+          T val = Ds[ci + jj * LD] - (mulc(y[ci], v[jj]) + mulc(v[ci], y[jj]));
+          if (ci == jj) val = from_re<T>(re_(val));
+          stcg_(&band[(ci - jj) + (long long)(p + jj) * ldb], val);
         }
-      }
-      __syncthreads();
       // ---- (iv) right update of the block below: creates the next bulge
-      const int p2 = p + len;
-      if (p2 < n) {
-        const int len2 = min(b, n - p2);
-        for (int idx = tid; idx < len2 * len; idx += NT) {
-          const int r = idx % len2, q = idx / len2;
-          Es[r + q * LD] = ldcg_(&band[(len + r - q) + (long long)(p + q) * ldb]);
-        }
-        __syncthreads();
-        for (int r = tid; r < len2; r += NT) {
+      if (len2 > 0) {
+        if (qi < len2) {  // w = tau E v: four partial sums per row
           T acc = zero_<T>();
-          for (int q = 0; q < len; ++q) acc += Es[r + q * LD] * v[q];
-          y[r] = tau * acc;
+          for (int q = qp; q < len; q += 4) acc += Es[qi + q * LD] * v[q];
+          part4[qp * 64 + qi] = acc;
         }
         __syncthreads();
-        for (int idx = tid; idx < len2 * len; idx += NT) {
-          const int r = idx % len2, q = idx / len2;
-          Es[r + q * LD] -= mulc(y[r], v[q]);
-        }
+        if (tid < len2) w[tid] = tau * ((part4[tid] + part4[64 + tid]) + (part4[128 + tid] + part4[192 + tid]));
+        __syncthreads();
+        if (ci < len2)
+          for (int q = cj; q < len; q += cstep) Es[ci + q * LD] -= mulc(w[ci], v[q]);
         pendingL = true;
       } else {
         pendingL = false;
@@ -381,7 +419,7 @@ __global__ void __launch_bounds__(BTF_COLS) k_bt_level_f32(int n, int k, int L, 
   }
 }
 
-template <class T> size_t bulge_smem(int b) { return sizeof(T) * ((size_t)3 * b * (b + 1) + 2 * b) + 64; }
+template <class T> size_t bulge_smem(int b) { return sizeof(T) * ((size_t)3 * b * (b + 1) + 3 * b + 4 * 64) + 64; }
 
 }  // namespace
 
