@@ -440,7 +440,12 @@ template <class T> int hb2st(Sys& s, double* d, double* e) {
     int per_sm = 0;
     GEV_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bulge<T>, NT, smem));
     if (per_sm < 1) return GEV_ERR_UNSUPPORTED;
+    // Sweep s+1 trails sweep s by three tasks and a sweep runs (n - s) / b tasks, so at most about
+    // n / (3b) sweeps are in flight: more blocks would only hold SMs (in a spin wait) that other
+    // streams' work - concurrent solves of the serving form - could use.
     int G = per_sm * s.sms;
+    const int inflight = n / (3 * b) + 8;
+    if (G > inflight) G = inflight;
     if (G > n - 2) G = n - 2;
     GEV_CUDA_TRY(cudaMemsetAsync(s.prog, 0, sizeof(int) * (size_t)n, s.stream));
     GEV_CUDA_TRY(cudaMemsetAsync(s.tau2, 0, s.es() * (size_t)n * s.ntask, s.stream));
