@@ -41,6 +41,7 @@ __device__ __forceinline__ float warp_sum(float v) {
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
   return v;
 }
+__device__ __forceinline__ zf warp_sum(zf v) { return make_zf(warp_sum(v.x), warp_sum(v.y)); }
 
 // Bounded acquire-wait until *flag >= target.  Thread 0 spins; returns false on timeout/abort.
 __device__ bool wait_ge(const int* flag, int target, int* status, int* abort_flag, int site) {
@@ -87,7 +88,7 @@ __device__ bool wait_ge(const int* flag, int target, int* status, int* abort_fla
 template <class T>
 __global__ void __launch_bounds__(NT) k_bulge(int n, int b, T* band, int ldb, T* V2, T* tau2, int ntask,
                                               int* progress, int* status, int* abort_flag) {
-  using R = typename std::conditional<std::is_same<T, float>::value, float, double>::type;
+  using R = typename real_of<T>::type;
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int PF = 64 * 64 / NT;  // register prefetch slots per thread (b <= 64)
   const int LD = b + 1;
@@ -255,17 +256,20 @@ __global__ void __launch_bounds__(NT) k_bulge(int n, int b, T* band, int ldb, T*
 // d = Re diag, e = |subdiag| with the phase recursion phi_0 = 1, phi_{i+1} = phi_i eps_i/|eps_i|
 // (complex), or e = subdiag (real).  One block: the phase recursion is sequential.
 template <class T>
-__global__ void k_tridiag_out(int n, const T* band, int ldb, double* d, double* e, T* phase) {
+// (the phases are formed in FP64 also from an FP32 band, so that their product over n steps stays
+// accurate)
+__global__ void k_tridiag_out(int n, const T* band, int ldb, double* d, double* e, zd* phase) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) d[i] = re_(band[(long long)i * ldb]);
   if constexpr (is_cx<T>::value) {
     if (threadIdx.x == 0) {
-      T ph = from_re<T>(1.0);
+      zd ph = make_zd(1.0, 0.0);
       phase[0] = ph;
       for (int i = 0; i + 1 < n; ++i) {
         const T eps = band[1 + (long long)i * ldb];
-        const double a = abs_(eps);
+        const double ex = re_(eps), ey = im_(eps);
+        const double a = hypot(ex, ey);
         e[i] = a;
-        if (a > 0.0) ph = ph * make_zd(eps.x / a, eps.y / a);
+        if (a > 0.0) ph = ph * make_zd(ex / a, ey / a);
         phase[i + 1] = ph;
       }
     }
@@ -276,15 +280,19 @@ __global__ void k_tridiag_out(int n, const T* band, int ldb, double* d, double* 
 
 // Y = D Z (real Z -> scalar type; D = diag(phase) for complex data, identity for real).
 template <class T>
-__global__ void k_phase_rows(int n, int k, const double* Z, long long ldz, const T* phase, T* Y,
+__global__ void k_phase_rows(int n, int k, const double* Z, long long ldz, const zd* phase, T* Y,
                              long long ldy) {
   const long long total = (long long)n * k;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(t % n), c = (int)(t / n);
     const double z = Z[i + c * ldz];
-    if constexpr (is_cx<T>::value) Y[i + c * ldy] = z * phase[i];
-    else Y[i + c * ldy] = z;
+    if constexpr (is_cx<T>::value) {
+      const zd v = z * phase[i];
+      Y[i + c * ldy] = T{(decltype(T{}.x))v.x, (decltype(T{}.x))v.y};
+    } else {
+      Y[i + c * ldy] = (T)z;
+    }
   }
 }
 
@@ -461,7 +469,7 @@ template <class T> int hb2st(Sys& s, double* d, double* e) {
     GEV_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_bulge<T>, dim3(G), dim3(NT), args, smem, s.stream));
   }
   GEV_COUNT(s);
-  k_tridiag_out<T><<<1, 256, 0, s.stream>>>(n, band, ldb, d, e, (T*)s.phase);
+  k_tridiag_out<T><<<1, 256, 0, s.stream>>>(n, band, ldb, d, e, (zd*)s.phase);
   GEV_TRY(last_error());
   s.have_tridiag_refl = true;
   return 0;
@@ -496,7 +504,7 @@ template <class T> int bt_hb2st(Sys& s, const double* Z, int ldz, int k, T* Y, i
     unsigned blocks = cdiv(total, 256);
     if (blocks > 16u * s.sms) blocks = 16u * s.sms;
     GEV_COUNT(s);
-    k_phase_rows<T><<<blocks, 256, 0, s.stream>>>(n, k, Z, ldz, (const T*)s.phase, Y, ldy);
+    k_phase_rows<T><<<blocks, 256, 0, s.stream>>>(n, k, Z, ldz, (const zd*)s.phase, Y, ldy);
     GEV_TRY(last_error());
   }
   if (n <= 2) return 0;
@@ -541,5 +549,7 @@ template int bt_hb2st<float>(Sys&, const double*, int, int, float*, int);
 template int hb2st<zd>(Sys&, double*, double*);
 template int bt_hb2st<double>(Sys&, const double*, int, int, double*, int);
 template int bt_hb2st<zd>(Sys&, const double*, int, int, zd*, int);
+template int hb2st<zf>(Sys&, double*, double*);
+template int bt_hb2st<zf>(Sys&, const double*, int, int, zf*, int);
 
 }  // namespace gev

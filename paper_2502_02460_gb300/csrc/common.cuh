@@ -32,6 +32,36 @@ __host__ __device__ __forceinline__ zd& operator-=(zd& a, zd b) { a.x -= b.x; a.
 __host__ __device__ __forceinline__ bool operator==(zd a, zd b) { return a.x == b.x && a.y == b.y; }
 __host__ __device__ __forceinline__ bool operator!=(zd a, zd b) { return !(a == b); }
 
+// complex64, interleaved (re, im): the FP32 stages of the complex mixed form
+struct alignas(8) zf {
+  float x, y;
+};
+
+__host__ __device__ __forceinline__ zf make_zf(float a, float b) { return zf{a, b}; }
+__host__ __device__ __forceinline__ zf operator+(zf a, zf b) { return {a.x + b.x, a.y + b.y}; }
+__host__ __device__ __forceinline__ zf operator-(zf a, zf b) { return {a.x - b.x, a.y - b.y}; }
+__host__ __device__ __forceinline__ zf operator-(zf a) { return {-a.x, -a.y}; }
+__host__ __device__ __forceinline__ zf operator*(zf a, zf b) {
+  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+__host__ __device__ __forceinline__ zf operator*(float s, zf a) { return {s * a.x, s * a.y}; }
+__host__ __device__ __forceinline__ zf operator*(zf a, float s) { return {s * a.x, s * a.y}; }
+__host__ __device__ __forceinline__ zf& operator+=(zf& a, zf b) { a.x += b.x; a.y += b.y; return a; }
+__host__ __device__ __forceinline__ zf& operator-=(zf& a, zf b) { a.x -= b.x; a.y -= b.y; return a; }
+__host__ __device__ __forceinline__ bool operator==(zf a, zf b) { return a.x == b.x && a.y == b.y; }
+__host__ __device__ __forceinline__ bool operator!=(zf a, zf b) { return !(a == b); }
+__host__ __device__ __forceinline__ zf conj_(zf a) { return {a.x, -a.y}; }
+__host__ __device__ __forceinline__ float re_(zf a) { return a.x; }
+__host__ __device__ __forceinline__ float im_(zf a) { return a.y; }
+__host__ __device__ __forceinline__ float abs2_(zf a) { return a.x * a.x + a.y * a.y; }
+__host__ __device__ __forceinline__ float abs_(zf a) { return hypotf(a.x, a.y); }
+__host__ __device__ __forceinline__ zf mulc(zf a, zf b) { return a * conj_(b); }
+__host__ __device__ __forceinline__ zf cmul(zf a, zf b) { return conj_(a) * b; }
+__host__ __device__ __forceinline__ zf div_(zf a, zf b) {
+  float d = b.x * b.x + b.y * b.y;
+  return {(a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d};
+}
+
 __host__ __device__ __forceinline__ float conj_(float a) { return a; }
 __host__ __device__ __forceinline__ float re_(float a) { return a; }
 __host__ __device__ __forceinline__ float im_(float) { return 0.0f; }
@@ -54,6 +84,7 @@ template <class T> __host__ __device__ __forceinline__ T from_re(double a);
 template <> __host__ __device__ __forceinline__ double from_re<double>(double a) { return a; }
 template <> __host__ __device__ __forceinline__ float from_re<float>(double a) { return (float)a; }
 template <> __host__ __device__ __forceinline__ zd from_re<zd>(double a) { return {a, 0.0}; }
+template <> __host__ __device__ __forceinline__ zf from_re<zf>(double a) { return {(float)a, 0.0f}; }
 template <class T> __host__ __device__ __forceinline__ T zero_() { return from_re<T>(0.0); }
 // a * conj(b) and conj(a) * b
 __host__ __device__ __forceinline__ double mulc(double a, double b) { return a * b; }
@@ -78,9 +109,19 @@ __device__ __forceinline__ void stcg_(double* p, double v) { __stcg(p, v); }
 __device__ __forceinline__ void stcg_(zd* p, zd v) {
   __stcg(reinterpret_cast<double2*>(p), make_double2(v.x, v.y));
 }
+__device__ __forceinline__ zf ldcg_(const zf* p) {
+  float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+  return make_zf(v.x, v.y);
+}
+__device__ __forceinline__ void stcg_(zf* p, zf v) { __stcg(reinterpret_cast<float2*>(p), make_float2(v.x, v.y)); }
 
 template <class T> struct is_cx { static constexpr bool value = false; };
 template <> struct is_cx<zd> { static constexpr bool value = true; };
+template <> struct is_cx<zf> { static constexpr bool value = true; };
+// real type of a scalar type, and the FP64 type of the same field
+template <class T> struct real_of { using type = double; };
+template <> struct real_of<float> { using type = float; };
+template <> struct real_of<zf> { using type = float; };
 
 // ------------------------------------------------------------------------- status word slots --
 enum StatusSlot {
@@ -187,6 +228,7 @@ struct Sys {
   double* R1 = nullptr;   // mixed form: n x n FP64 refinement buffers (R1..R3)
   double* R2 = nullptr;
   double* R3 = nullptr;
+  double* R4 = nullptr;   // complex mixed form: the k x k Gram and coefficient matrices
   void* sub = nullptr;    // mixed form: handle of the k x k Rayleigh-Ritz pencil (gev_sys*)
   int emu_fp64 = 0;       // 1: real FP64 GEMMs formed on the tensor cores (ozaki.cu)
   int fp32_tc = 0;        // FP32 GEMMs: 6 / 3 = BF16x6 / BF16x3 tensor products when large (tc_gemm.cu), 0 = CUDA cores
@@ -290,6 +332,8 @@ int sync_status(Sys& s);  // synchronise the stream, copy the status words to th
 // mixed form (mixed.cu): FP32 reduction, FP64 Ogita-Aishima refinement of the standard problem
 int solve_mixed(Sys& s, const double* H, int ldh, const double* S, int lds, int k, double* evals,
                 double* C, int ldc, gev_report* rep);
+int solve_mixed_cx(Sys& s, const zd* H, int ldh, const zd* S, int lds, int k, double* evals, zd* C, int ldc,
+                   gev_report* rep);
 
 inline void step_mark(Sys& s, int step) {
   if (!s.opts.timing || s.n_marks >= 2 * GEV_NSTEPS + 2) return;

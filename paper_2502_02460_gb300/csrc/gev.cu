@@ -69,7 +69,8 @@ size_t carve(Sys& s, char* base) {
   if (s.fp32_tc) ozb = std::max(ozb, gemm_tc32_scratch((int)n, (int)n, (int)n));
   size_t ooz = L.add(ozb);
   const bool mixed = s.opts.prec == GEV_MIXED;
-  size_t oR1 = L.add(mixed ? n * n * 8 : 8), oR2 = L.add(mixed ? n * n * 8 : 8), oR3 = L.add(mixed ? n * n * 8 : 8);
+  size_t oR1 = L.add(mixed ? n * n * es : 8), oR2 = L.add(mixed ? n * n * es : 8), oR3 = L.add(mixed ? n * n * es : 8);
+  size_t oR4 = L.add(mixed && s.dtype == GEV_C128 ? 3 * n * n * es : 8);
   if (base) {
     s.A = base + oA; s.X = base + oX; s.W1 = base + oW1; s.V1 = base + oV1; s.T1 = base + oT1;
     s.dinv = base + odinv; s.Pn = base + oPn; s.small = base + osmall;
@@ -89,6 +90,7 @@ size_t carve(Sys& s, char* base) {
     s.R1 = (double*)(base + oR1);
     s.R2 = (double*)(base + oR2);
     s.R3 = (double*)(base + oR3);
+    s.R4 = (double*)(base + oR4);
   }
   return L.total;
 }
@@ -244,8 +246,9 @@ int gev_solve(gev_sys* h, const void* H, int ldh, const void* S, int lds, int k,
   if (cudaSetDevice(s.opts.device) != cudaSuccess) return GEV_ERR_CUDA;
   if (rep) std::memset(rep, 0, sizeof(*rep));
   int r;
-  if (s.opts.prec == GEV_MIXED && s.dtype == GEV_C128) return GEV_ERR_UNSUPPORTED;
-  if (s.dtype == GEV_C128)
+  if (s.opts.prec == GEV_MIXED && s.dtype == GEV_C128)
+    r = solve_mixed_cx(s, (const zd*)H, ldh, (const zd*)S, lds, k, evals, (zd*)C, ldc, rep);
+  else if (s.dtype == GEV_C128)
     r = solve_t<zd>(s, (const zd*)H, ldh, (const zd*)S, lds, k, evals, (zd*)C, ldc, rep);
   else if (s.opts.prec == GEV_MIXED)
     r = solve_mixed(s, (const double*)H, ldh, (const double*)S, lds, k, evals, (double*)C, ldc, rep);

@@ -93,7 +93,12 @@ __global__ void k_convert2d(int m, int n, const TA* __restrict__ src, long long 
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
     int i = (int)(t % m), j = (int)(t / m);
-    dst[i + j * ldd] = (TB)src[i + j * lds];
+    if constexpr (is_cx<TB>::value) {
+      const TA a = src[i + j * lds];
+      dst[i + j * ldd] = TB{(decltype(TB{}.x))a.x, (decltype(TB{}.x))a.y};
+    } else {
+      dst[i + j * ldd] = (TB)src[i + j * lds];
+    }
   }
 }
 
@@ -202,6 +207,8 @@ int convert2d(Sys& s, int m, int n, const TA* src, long long lds, TB* dst, long 
 }
 template int convert2d<double, float>(Sys&, int, int, const double*, long long, float*, long long);
 template int convert2d<float, double>(Sys&, int, int, const float*, long long, double*, long long);
+template int convert2d<zd, zf>(Sys&, int, int, const zd*, long long, zf*, long long);
+template int convert2d<zf, zd>(Sys&, int, int, const zf*, long long, zd*, long long);
 
 template <class T> int normalize_phase(Sys& s, int n, int k, T* C, int ldc) {
   if (n <= 0 || k <= 0) return 0;

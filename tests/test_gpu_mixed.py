@@ -79,13 +79,25 @@ def test_mixed_reuse_factor(dev):
     assert np.max(np.abs(w - p.lam[:k])) <= 1e-11 * norm1(p.H)
 
 
-def test_mixed_complex_not_available(dev):
-    n = 20
-    p = inputs.make_problem(n, 5, seed=1, complex_=True)
+@pytest.mark.parametrize("n,k,cluster", [(1, 1, False), (40, 40, False), (200, 50, False), (333, 333, False),
+                                         (700, 175, True), (1100, 300, False)])
+def test_mixed_complex_matches_oracle(dev, n, k, cluster):
+    """Complex Hermitian pencils through the mixed form (FP64 reduction to the band, complex64 bulge
+    chasing, divide-and-conquer products and back-transform 2, FP64 Hermitian refinement): the same
+    bounds as the real mixed form, with a 1e-8 cluster of 16 inside the wanted set in one case."""
+    p = inputs.make_problem(n, k, seed=800 + n, complex_=True, cluster=cluster)
     with gv().Solver(n, complex_=True, device=dev, mixed=True) as s:
-        with pytest.raises(gv().GevError) as ei:
-            s.solve_cm(gv().cm_from_numpy(p.H, dev), gv().cm_from_numpy(p.S, dev), 5)
-        assert ei.value.code == 7
+        w, Cb = s.solve_cm(gv().cm_from_numpy(inputs.lower_only(p.H, 2.0), dev),
+                           gv().cm_from_numpy(inputs.lower_only(p.S, -2.0), dev), k)
+        w, C, rep = w.cpu().numpy(), gv().numpy_from_cm(Cb), s.last_report
+    wo, Co, info, _ = oracle.gev(p.H, p.S, k)
+    h1 = norm1(p.H)
+    assert np.max(np.abs(w - wo)) <= 1e-11 * h1
+    assert np.max(np.abs(w - p.lam[:k])) <= 1e-11 * h1
+    r, o = oracle.check(p.H, p.S, w, C)
+    assert r <= 1e-11, r
+    assert o <= 1e-12 * np.sqrt(n), o
+    assert rep["refine_iters"] <= 5 and rep["refine_resid"] <= 1e-11
 
 
 @pytest.mark.parametrize("n,k,cluster", [(1500, 400, False), (1200, 300, True)])
