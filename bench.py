@@ -154,7 +154,7 @@ def run_reference(args):
     return 0
 
 
-def run_stream(args, dev):
+def run_stream(args, dev, mixed=False):
     """A prefix of the k-point serving stream (Poisson arrivals at 200/s, complex128 pencils of
     log-uniform size recurring for 10 SCF iterations with fixed S, k = N/4) through the
     continuous-batching server; latency from each request's scheduled arrival to its result."""
@@ -177,7 +177,7 @@ def run_stream(args, dev):
         H = p.H + (spec.dh_rel * np.linalg.norm(p.H) / np.linalg.norm(dH) * dH if it > 0 else 0)
         cache[(sid, it)] = gev.cm_from_numpy(H, dev)
     torch.cuda.synchronize()
-    srv = serve.Server(budget_bytes=120e9, workers=6, device=dev, mixed=False)
+    srv = serve.Server(budget_bytes=120e9, workers=6, device=dev, mixed=mixed)
     t0 = time.perf_counter()
     futs = []
     for (t, sid, it, n, k, last) in plan:
@@ -190,7 +190,8 @@ def run_stream(args, dev):
         f.result()
     srv.close()
     st = srv.stats()
-    st.update({"precision": "plain FP64", "dtype": "c128",
+    st.update({"precision": "mixed (FP32 band reduction + FP64 refinement)" if mixed else "plain FP64",
+               "dtype": "c128",
                "workload": f"first {spec.requests} requests of the k-point stream (Poisson 200/s, "
                            f"N log-uniform in [{spec.n_min}, {spec.n_max}], 10 SCF iterations per "
                            f"system, S fixed, k = N/4)"})
@@ -373,11 +374,12 @@ def main():
             torch.distributed.barrier()
         return 0
     cb = None if args.no_cpu_baseline else cpu_baseline(args.n, args.k, args.complex)
-    stream_stats = None
+    stream_stats = stream_mixed = None
     if args.stream_requests > 0 and ws == 1:
         del solver, Hb, Sb
         torch.cuda.empty_cache()
         stream_stats = run_stream(args, dev)
+        stream_mixed = run_stream(args, dev, mixed=True)
     value = ms / 1e3 / (1 if ws == 1 else 1)  # seconds per solve (each rank solves one system)
     line = {
         "metric": METRIC, "value": value, "unit": "s", "n_gpus": ws, "steps": args.steps,
@@ -391,6 +393,7 @@ def main():
         "refine": {"iterations": reps[-1]["refine_iters"], "residual": reps[-1]["refine_resid"]}
         if args.mixed else None,
         "stream": stream_stats,
+        "stream_mixed": stream_mixed,
         "roofline": {"bound": "tensor", "kernel": roof_kernel,
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": None,

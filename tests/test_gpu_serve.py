@@ -65,3 +65,35 @@ def test_stream_results_in_the_mix_equal_results_alone(dev):
         assert torch.equal(w, wa) and torch.equal(Cb, Ca), (sid, t)
         wo, _, info, _ = oracle.gev(Hs[t], S, k)
         assert np.max(np.abs(w.cpu().numpy() - wo)) <= 1e-11 * norm1(Hs[t])
+
+
+def test_mixed_stream_results_in_the_mix_equal_results_alone(dev):
+    """The serving form in mixed precision (complex pencils through the mixed form): each result in
+    the mix equals the result computed alone, bit for bit, and meets the oracle's eigenvalue bound."""
+    import torch
+
+    from paper_2502_02460_gb300 import gev, serve
+
+    sizes = {0: 120, 1: 64, 2: 180}
+    iters = 2
+    data = {sid: scf_inputs(n, sid, iters) for sid, n in sizes.items()}
+    srv = serve.Server(budget_bytes=40e9, workers=3, device=dev, mixed=True)
+    futs = {}
+    for t in range(iters):
+        for sid, n in sizes.items():
+            S, Hs = data[sid]
+            k = max(1, n // 4)
+            Sb = gev.cm_from_numpy(S, dev) if t == 0 else None
+            futs[(sid, t)] = srv.submit(sid, gev.cm_from_numpy(Hs[t], dev), Sb, k, n=n, complex_=True,
+                                        last=(t == iters - 1))
+    res = {key: f.result(timeout=300) for key, f in futs.items()}
+    srv.close()
+    for (sid, t), (w, Cb, rep) in res.items():
+        n = sizes[sid]
+        k = max(1, n // 4)
+        S, Hs = data[sid]
+        with gev.Solver(n, complex_=True, device=dev, mixed=True) as s:
+            wa, Ca = s.solve_cm(gev.cm_from_numpy(Hs[t], dev), gev.cm_from_numpy(S, dev), k)
+        assert torch.equal(w, wa) and torch.equal(Cb, Ca), (sid, t)
+        wo, _, info, _ = oracle.gev(Hs[t], S, k)
+        assert np.max(np.abs(w.cpu().numpy() - wo)) <= 1e-11 * norm1(Hs[t])
