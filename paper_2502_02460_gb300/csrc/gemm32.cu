@@ -161,6 +161,8 @@ __global__ void splitk_reduce32(G32<TI, TO> p) {
 template <class TI, class TO> void gemm32(Sys& s, const GemmP<TI>& q, TO* C, float alpha, float beta) {
   if (q.M <= 0 || q.N <= 0) return;
   // large products go to the tensor cores (BF16 split products, tc_gemm.cu) when enabled
+  // (thin products stay on the CUDA cores: the tensor cores' FP32 accumulation is about ten times
+  // less accurate over long K, which costs the mixed form refinement iterations)
   if (s.fp32_tc && q.M >= 128 && q.N >= 128 && q.K >= 32 && (double)q.M * q.N * q.K >= 1.0e8 &&
       gemm_tc32<TI, TO>(s, q, C, alpha, beta, s.fp32_tc))
     return;
