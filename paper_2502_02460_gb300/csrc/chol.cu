@@ -183,6 +183,53 @@ template <class T> int trtri(Sys& s, T* A, int lda) {
   return last_error();
 }
 
+// Cholesky factorisation and inversion in one recursion: A (lower triangle of S = L L^H) <- X = L^{-1}.
+//   X11 = L11^{-1}                       (recursion on the leading block)
+//   L21 = A21 X11^H,  A22 <- A22 - L21 L21^H (lower)
+//   X22 = L22^{-1}                       (recursion on the trailing block)
+//   X21 = -X22 (L21 X11)
+// Every product is a large triangular GEMM (the flat blocked algorithm's are K = nb wide); leaves of
+// nb factor and invert a diagonal block.  L itself is not kept.  W: n x n scratch.
+template <class T> void potrf_inv_rec(Sys& s, T* A, int lda, int o, int sz, T* W) {
+  const int nb = s.nb;
+  T* Aoo = A + o + (long long)o * lda;
+  if (sz <= nb) {
+    GEV_COUNT(s);
+    k_potrf_diag<T><<<1, 256, diag_smem<T>(), s.stream>>>(sz, Aoo, lda, (T*)s.dinv, nb, s.status, o);
+    copy2d<T>(s, sz, sz, (T*)s.dinv, nb, Aoo, lda);
+    return;
+  }
+  int n1 = (sz / 2 + nb - 1) / nb * nb;
+  if (n1 >= sz) n1 = sz - nb;
+  const int n2 = sz - n1;
+  potrf_inv_rec(s, A, lda, o, n1, W);
+  T* X11 = Aoo;
+  T* A21 = A + (o + n1) + (long long)o * lda;
+  T* A22 = A + (o + n1) + (long long)(o + n1) * lda;
+  const T one = from_re<T>(1.0), mone = from_re<T>(-1.0), zero = zero_<T>();
+  GemmP<T> g = gp<T>(n2, n1, n1, 0, 2, one, A21, lda, X11, lda, zero, W, s.n);  // L21 = A21 X11^H
+  g.tri_b = 2;
+  gemm(s, g);
+  g = gp<T>(n2, n2, n1, 0, 2, mone, W, s.n, W, s.n, one, A22, lda);             // A22 -= L21 L21^H
+  g.c_lower = 1;
+  gemm(s, g);
+  copy2d<T>(s, n2, n1, W, s.n, A21, lda);
+  potrf_inv_rec(s, A, lda, o + n1, n2, W);
+  g = gp<T>(n2, n1, n1, 0, 0, one, A21, lda, X11, lda, zero, W, s.n);           // W = L21 X11
+  g.tri_b = 1;
+  gemm(s, g);
+  g = gp<T>(n2, n1, n2, 0, 0, mone, A + (o + n1) + (long long)(o + n1) * lda, lda, W, s.n, zero, A21, lda);
+  g.tri_a = 1;                                                                   // X21 = -X22 W
+  gemm(s, g);
+}
+
+template <class T> int potrf_inv(Sys& s, T* A, int lda) {
+  GEV_TRY(set_smem_attrs<T>());
+  potrf_inv_rec<T>(s, A, lda, 0, s.n, (T*)s.W1);
+  GEV_TRY(zero_upper<T>(s, s.n, A, lda));
+  return last_error();
+}
+
 template <class T> int hegst(Sys& s, const T* H, int ldh, const T* X, int ldx, T* A, int lda) {
   const int n = s.n;
   T* B = (T*)s.W1;
@@ -213,6 +260,7 @@ template <class T> int mult(Sys& s, const T* X, int ldx, const T* Y, int ldy, in
 
 #define GEV_INST(T)                                                     \
   template int potrf<T>(Sys&, T*, int);                                 \
+  template int potrf_inv<T>(Sys&, T*, int);                             \
   template int trtri<T>(Sys&, T*, int);                                 \
   template int hegst<T>(Sys&, const T*, int, const T*, int, T*, int);   \
   template int mult<T>(Sys&, const T*, int, const T*, int, int, T*, int);

@@ -307,6 +307,7 @@ template <class F> int allow_max_dyn_smem(F* func) {
 }
 
 // ---------------------------------------------------------------------------- step launchers --
+template <class T> int potrf_inv(Sys& s, T* A, int lda);  // S (lower) -> L^{-1}, one recursion
 template <class T> int potrf(Sys& s, T* A, int lda);
 template <class T> int trtri(Sys& s, T* A, int lda);
 template <class T> int hegst(Sys& s, const T* H, int ldh, const T* X, int ldx, T* A, int lda);

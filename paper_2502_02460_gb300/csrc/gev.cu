@@ -398,7 +398,8 @@ template <class T> int solve_t(Sys& s, const T* H, int ldh, const T* S, int lds,
   if (!reuse) {
     // steps 1-2: X = L^{-1}, S = L L^H
     GEV_TRY(copy_lower<T>(s, n, S, lds, X, n));
-    GEV_TRY(potrf<T>(s, X, n));
+    // Cholesky and inversion in one recursion (the "invert" step time is included in "cholesky")
+    GEV_TRY(potrf_inv<T>(s, X, n));
     GEV_TRY(sync_status(s));
     if (s.status_h[ST_NOT_SPD]) {
       if (rep) rep->info = s.status_h[ST_NOT_SPD];
@@ -406,7 +407,6 @@ template <class T> int solve_t(Sys& s, const T* H, int ldh, const T* S, int lds,
       return GEV_ERR_NOT_SPD;
     }
     mark(GEV_STEP_INVERT);
-    GEV_TRY(trtri<T>(s, X, n));
   } else {
     mark(GEV_STEP_INVERT);
   }

@@ -111,7 +111,7 @@ __global__ void k_scale_w(int m, int k, float* W, long long ldw, const double* l
 }
 
 // One Ogita-Aishima step in span(Y) (their Algorithm 1 on the Gram data T = Y^T A Y,
-// G = Y^T Y, both taken symmetric): lambda_i = T_ii / G_ii and W = I + E with
+// G = Y^T Y, lower triangles): lambda_i = T_ii / G_ii and W = I + E with
 //   e_ii = (1 - G_ii) / 2,
 //   e_ij = (T_ij - lambda_j G_ij) / (lambda_j - lambda_i)   if |lambda_j - lambda_i| > delta,
 //   e_ij = -G_ij / 2                                          otherwise.
@@ -130,10 +130,10 @@ __global__ void k_oa_step(int k, const double* T, const double* G, double delta,
       W[t] = 1.0 + e;
       lam[i] = li;
     } else {
-      // symmetric parts: the rounding asymmetry of the products, divided by small gaps, would
-      // otherwise break e_ij + e_ji = -G_ij (first-order orthogonality)
-      const long long tt = j + (long long)i * k;
-      const double tij = 0.5 * (T[t] + T[tt]), gij = 0.5 * (G[t] + G[tt]);
+      // T and G hold their lower triangles only (exactly symmetric data: the rounding asymmetry of
+      // the products, divided by small gaps, would otherwise break e_ij + e_ji = -G_ij)
+      const long long tl = (i > j) ? t : j + (long long)i * k;
+      const double tij = T[tl], gij = G[tl];
       const double lj = T[j + (long long)j * k] / G[j + (long long)j * k];
       const double gap = lj - li;
       e = (fabs(gap) > delta) ? (tij - lj * gij) / gap : -0.5 * gij;
@@ -145,14 +145,14 @@ __global__ void k_oa_step(int k, const double* T, const double* G, double delta,
   if ((threadIdx.x & 31) == 0) atomicMax(emax, (unsigned long long)__double_as_longlong(m));
 }
 
-// First-order Loewdin orthonormalisation from G = Y^T Y: W = I + (I - G_sym) / 2, so that
+// First-order Loewdin orthonormalisation from G = Y^T Y (lower triangle): W = I + (I - G) / 2, so that
 // (Y W)^T (Y W) = I + O((G - I)^2).  One block per column j; *dmax receives the largest column
 // 1-norm of G - I (bit pattern of a non-negative double, atomicMax).
 __global__ void k_lowdin(int k, const double* G, double* W, unsigned long long* dmax) {
   const int j = blockIdx.x;
   double s = 0.0;
   for (int i = threadIdx.x; i < k; i += blockDim.x) {
-    const double g = 0.5 * (G[i + (long long)j * k] + G[j + (long long)i * k]);
+    const double g = (i >= j) ? G[i + (long long)j * k] : G[j + (long long)i * k];  // lower triangle
     const double d = (i == j ? 1.0 : 0.0) - g;
     W[i + (long long)j * k] = (i == j ? 1.0 : 0.0) + 0.5 * d;
     s += fabs(d);
@@ -221,7 +221,7 @@ __global__ void k_scale_w_z(int m, int k, zd* W, long long ldw, const double* la
   }
 }
 
-// Ogita-Aishima step on Hermitian Gram data (T, G taken Hermitian): lambda_i = Re T_ii / Re G_ii,
+// Ogita-Aishima step on Hermitian Gram data (lower triangles): lambda_i = Re T_ii / Re G_ii,
 // e_ii = (1 - Re G_ii) / 2, e_ij = (T_ij - lambda_j G_ij) / (lambda_j - lambda_i) or -G_ij / 2
 __global__ void k_oa_step_z(int k, const zd* T, const zd* G, double delta, zd* W, double* lam,
                             unsigned long long* emax) {
@@ -238,8 +238,9 @@ __global__ void k_oa_step_z(int k, const zd* T, const zd* G, double delta, zd* W
       lam[i] = li;
       ea = fabs(e);
     } else {
-      const long long tt = j + (long long)i * k;
-      const zd tij = 0.5 * (T[t] + conj_(T[tt])), gij = 0.5 * (G[t] + conj_(G[tt]));
+      const bool lo = i > j;  // lower triangles only: the upper entries are the conjugates
+      const long long tl = lo ? t : j + (long long)i * k;
+      const zd tij = lo ? T[tl] : conj_(T[tl]), gij = lo ? G[tl] : conj_(G[tl]);
       const double lj = T[j + (long long)j * k].x / G[j + (long long)j * k].x;
       const double gap = lj - li;
       const zd e = (fabs(gap) > delta) ? (1.0 / gap) * (tij - lj * gij) : -0.5 * gij;
@@ -256,7 +257,7 @@ __global__ void k_lowdin_z(int k, const zd* G, zd* W, unsigned long long* dmax) 
   const int j = blockIdx.x;
   double s = 0.0;
   for (int i = threadIdx.x; i < k; i += blockDim.x) {
-    const zd g = 0.5 * (G[i + (long long)j * k] + conj_(G[j + (long long)i * k]));
+    const zd g = (i >= j) ? G[i + (long long)j * k] : conj_(G[j + (long long)i * k]);  // lower triangle
     const zd d = make_zd(i == j ? 1.0 : 0.0, 0.0) - g;
     W[i + (long long)j * k] = make_zd(i == j ? 1.0 : 0.0, 0.0) + 0.5 * d;
     s += abs_(d);
@@ -291,7 +292,8 @@ int solve_mixed(Sys& s, const double* H, int ldh, const double* S, int lds, int 
   const bool reuse = (S == nullptr);
   if (!reuse) {
     GEV_TRY(copy_lower<double>(s, n, S, lds, X, n));
-    GEV_TRY(potrf<double>(s, X, n));
+    // Cholesky and inversion in one recursion (the "invert" step time is included in "cholesky")
+    GEV_TRY(potrf_inv<double>(s, X, n));
     GEV_TRY(sync_status(s));
     if (s.status_h[ST_NOT_SPD]) {
       if (rep) rep->info = s.status_h[ST_NOT_SPD];
@@ -299,7 +301,6 @@ int solve_mixed(Sys& s, const double* H, int ldh, const double* S, int lds, int 
       return GEV_ERR_NOT_SPD;
     }
     mark(GEV_STEP_INVERT);
-    GEV_TRY(trtri<double>(s, X, n));
   }
   if (rep) rep->reused_factor = reuse ? 1 : 0;
   mark(GEV_STEP_MULTIPLY);
@@ -380,8 +381,14 @@ int solve_mixed(Sys& s, const double* H, int ldh, const double* S, int lds, int 
   constexpr double kOaCluster = 1e-7;
   for (;; ++it) {
     gemm(s, gp<double>(n, k, n, 0, 0, 1.0, A, n, Yd, n, 0.0, AY, n));   // AY = A Y
-    gemm(s, gp<double>(k, k, n, 1, 0, 1.0, Yd, n, AY, n, 0.0, T, k));   // T = Y^T A Y
-    gemm(s, gp<double>(k, k, n, 1, 0, 1.0, Yd, n, Yd, n, 0.0, G, k));   // G = Y^T Y
+    {  // T = Y^T A Y, G = Y^T Y: lower triangles
+      GemmP<double> g = gp<double>(k, k, n, 1, 0, 1.0, Yd, n, AY, n, 0.0, T, k);
+      g.c_lower = 1;
+      gemm(s, g);
+      g = gp<double>(k, k, n, 1, 0, 1.0, Yd, n, Yd, n, 0.0, G, k);
+      g.c_lower = 1;
+      gemm(s, g);
+    }
     // after the first iteration the basis is close to the eigenvectors: one Ogita-Aishima step in
     // span(Y) replaces the Rayleigh-Ritz solve while its corrections stay small
     bool oa = false;
@@ -418,7 +425,11 @@ int solve_mixed(Sys& s, const double* H, int ldh, const double* S, int lds, int 
     if (resid <= tol) {
       // an Ogita-Aishima step leaves second-order defects in orthogonality: finish with a
       // first-order Loewdin step; it moves the residuals by at most ||A|| max_j sum_i |G - I|_ij
-      gemm(s, gp<double>(k, k, n, 1, 0, 1.0, Yd, n, Yd, n, 0.0, G, k));
+      {
+        GemmP<double> g = gp<double>(k, k, n, 1, 0, 1.0, Yd, n, Yd, n, 0.0, G, k);
+        g.c_lower = 1;
+        gemm(s, g);
+      }
       GEV_CUDA_TRY(cudaMemsetAsync(scal + 3, 0, sizeof(double), st));
       GEV_COUNT(s);
       k_lowdin<<<k, 256, 0, st>>>(k, G, W, (unsigned long long*)(scal + 3));
@@ -492,7 +503,8 @@ int solve_mixed_cx(Sys& s, const zd* H, int ldh, const zd* S, int lds, int k, do
   const bool reuse = (S == nullptr);
   if (!reuse) {
     GEV_TRY(copy_lower<zd>(s, n, S, lds, X, n));
-    GEV_TRY(potrf<zd>(s, X, n));
+    // Cholesky and inversion in one recursion (the "invert" step time is included in "cholesky")
+    GEV_TRY(potrf_inv<zd>(s, X, n));
     GEV_TRY(sync_status(s));
     if (s.status_h[ST_NOT_SPD]) {
       if (rep) rep->info = s.status_h[ST_NOT_SPD];
@@ -500,7 +512,6 @@ int solve_mixed_cx(Sys& s, const zd* H, int ldh, const zd* S, int lds, int k, do
       return GEV_ERR_NOT_SPD;
     }
     mark(GEV_STEP_INVERT);
-    GEV_TRY(trtri<zd>(s, X, n));
   }
   if (rep) rep->reused_factor = reuse ? 1 : 0;
   mark(GEV_STEP_MULTIPLY);
@@ -582,8 +593,14 @@ int solve_mixed_cx(Sys& s, const zd* H, int ldh, const zd* S, int lds, int k, do
   bool converged = false;
   for (;; ++it) {
     gemm(s, gp<zd>(n, k, n, 0, 0, one, A, n, Yd, n, zero, AY, n));   // AY = A Y
-    gemm(s, gp<zd>(k, k, n, 2, 0, one, Yd, n, AY, n, zero, T, k));   // T = Y^H A Y
-    gemm(s, gp<zd>(k, k, n, 2, 0, one, Yd, n, Yd, n, zero, G, k));   // G = Y^H Y
+    {  // T = Y^H A Y, G = Y^H Y: lower triangles
+      GemmP<zd> g = gp<zd>(k, k, n, 2, 0, one, Yd, n, AY, n, zero, T, k);
+      g.c_lower = 1;
+      gemm(s, g);
+      g = gp<zd>(k, k, n, 2, 0, one, Yd, n, Yd, n, zero, G, k);
+      g.c_lower = 1;
+      gemm(s, g);
+    }
     bool oa = false;
     if (it > 0 && !s.opts.refine_rr_only) {
       double emax = 0.0;
@@ -616,7 +633,11 @@ int solve_mixed_cx(Sys& s, const zd* H, int ldh, const zd* S, int lds, int k, do
     std::swap(Yd, Yn);
     if (resid <= tol && !oa) { converged = true; break; }
     if (resid <= tol) {  // Loewdin finish after an Ogita-Aishima step (see solve_mixed)
-      gemm(s, gp<zd>(k, k, n, 2, 0, one, Yd, n, Yd, n, zero, G, k));
+      {
+        GemmP<zd> g = gp<zd>(k, k, n, 2, 0, one, Yd, n, Yd, n, zero, G, k);
+        g.c_lower = 1;
+        gemm(s, g);
+      }
       GEV_CUDA_TRY(cudaMemsetAsync(scal + 3, 0, sizeof(double), st));
       GEV_COUNT(s);
       k_lowdin_z<<<k, 256, 0, st>>>(k, G, W, (unsigned long long*)(scal + 3));
