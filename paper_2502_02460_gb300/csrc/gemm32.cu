@@ -2,10 +2,10 @@
 // the back-transforms and the divide-and-conquer merge products.  Operands may be FP32 or FP64
 // (converted to FP32 when staged), the result FP32 or FP64.
 //
-// 128x128 tile, 8-deep k slice, 256 threads with an 8x8 register micro-tile each (rows
-// ty*4+{0..3} and 64+ty*4+{0..3}, columns likewise, so the shared-memory reads are float4 and
-// conflict free), a two-stage smem pipeline, the same zero-pattern masks as the FP64 GEMM and a
-// deterministic split K.  Measured FFMA peak on GB300: 73.9 TFLOP/s.
+// 128x128 tile (128x64 / 64x128 for thin products), 8-deep k slice, an 8x8 register micro-tile per
+// thread (rows ty*4+{0..3} and BM/2+ty*4+{0..3}, columns likewise, so the shared-memory reads are
+// float4 and conflict free), a two-stage smem pipeline, the same zero-pattern masks as the FP64
+// GEMM and a deterministic split K.  Measured FFMA peak on GB300: 73.9 TFLOP/s.
 #include <algorithm>
 
 #include "common.cuh"
@@ -14,7 +14,7 @@ namespace gev {
 
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 8, NT = 256;
+constexpr int BK = 8;
 
 template <class TI, class TO> struct G32 {
   int M, N, K, ta, tb, tri_a, tri_b, c_lower;
@@ -42,8 +42,11 @@ __device__ __forceinline__ float ld_b(const G32<TI, TO>& p, int gk, int gj, int 
   return (float)((p.tb == 0) ? p.B[gk + gj * p.ldb] : p.B[gj + gk * p.ldb]);
 }
 
-template <class TI, class TO>
-__global__ void __launch_bounds__(NT) gemm32_kernel(G32<TI, TO> p) {
+// BM x BN tile (128 x 128, or 128 x 64 / 64 x 128 for thin products), BM BN / 64 threads with an
+// 8 x 8 register micro-tile each: rows ty*4+{0..3} and BM/2+ty*4+{0..3}, columns likewise.
+template <class TI, class TO, int BM, int BN>
+__global__ void __launch_bounds__(BM * BN / 64) gemm32_kernel(G32<TI, TO> p) {
+  constexpr int NT = BM * BN / 64, RA = BM * BK / NT, RB = BN * BK / NT, TXN = BN / 8;
   __shared__ __align__(16) float As[2][BK][BM];
   __shared__ __align__(16) float Bs[2][BK][BN];
   const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
@@ -60,20 +63,24 @@ __global__ void __launch_bounds__(NT) gemm32_kernel(G32<TI, TO> p) {
     ke = min(ke, z0 + chunk);
   }
   kb = kb / BK * BK;
-  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const int tid = threadIdx.x, tx = tid % TXN, ty = tid / TXN;
   float acc[8][8];
 #pragma unroll
   for (int i = 0; i < 8; ++i)
 #pragma unroll
     for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
-  float ra[4], rb[4];
+  float ra[RA], rb[RB];
   auto fetch = [&](int k0) {
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
+    for (int r = 0; r < RA; ++r) {
       const int e = tid + r * NT;
       int i, k;
       if (p.ta == 0) { i = e % BM; k = e / BM; } else { k = e % BK; i = e / BK; }
       ra[r] = ld_a(p, m0 + i, k0 + k, kb, ke);
+    }
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+      const int e = tid + r * NT;
       int j, kk;
       if (p.tb == 0) { kk = e % BK; j = e / BK; } else { j = e % BN; kk = e / BN; }
       rb[r] = ld_b(p, k0 + kk, n0 + j, kb, ke);
@@ -81,11 +88,15 @@ __global__ void __launch_bounds__(NT) gemm32_kernel(G32<TI, TO> p) {
   };
   auto stash = [&](int buf) {
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
+    for (int r = 0; r < RA; ++r) {
       const int e = tid + r * NT;
       int i, k;
       if (p.ta == 0) { i = e % BM; k = e / BM; } else { k = e % BK; i = e / BK; }
       As[buf][k][i] = ra[r];
+    }
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+      const int e = tid + r * NT;
       int j, kk;
       if (p.tb == 0) { kk = e % BK; j = e / BK; } else { j = e % BN; kk = e / BN; }
       Bs[buf][kk][j] = rb[r];
@@ -103,9 +114,9 @@ __global__ void __launch_bounds__(NT) gemm32_kernel(G32<TI, TO> p) {
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4]);
-      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][64 + ty * 4]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][BM / 2 + ty * 4]);
       const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
-      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][64 + tx * 4]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][BN / 2 + tx * 4]);
       const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
       const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
@@ -119,22 +130,28 @@ __global__ void __launch_bounds__(NT) gemm32_kernel(G32<TI, TO> p) {
       buf ^= 1;
     }
   }
+  // epilogue: the 8 loads of C of a row first, so that they overlap
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
-    const int gi = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+    const int gi = m0 + (i < 4 ? ty * 4 + i : BM / 2 + ty * 4 + (i - 4));
     if (gi >= p.M) continue;
+    const bool read_c = p.ksplit == 1 && p.beta != 0.f;
+    TO cin[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      const int gj = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4));
+      const int gj = n0 + (j < 4 ? tx * 4 + j : BN / 2 + tx * 4 + (j - 4));
+      cin[j] = (read_c && gj < p.N && !(p.c_lower && gi < gj)) ? p.C[gi + gj * p.ldc] : (TO)0;
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int gj = n0 + (j < 4 ? tx * 4 + j : BN / 2 + tx * 4 + (j - 4));
       if (gj >= p.N) continue;
       if (p.c_lower && gi < gj) continue;
       if (p.ksplit > 1) {
         p.ws[(size_t)blockIdx.z * p.M * p.N + gi + (size_t)gj * p.M] = acc[i][j];
       } else {
-        TO* c = &p.C[gi + gj * p.ldc];
         const TO out = (TO)(p.alpha * acc[i][j]);  // the accumulation with C happens in TO
-        if (p.beta != 0.f) *c = out + (TO)p.beta * (*c);
-        else *c = out;
+        p.C[gi + gj * p.ldc] = read_c ? out + (TO)p.beta * cin[j] : out;
       }
     }
   }
@@ -170,6 +187,9 @@ template <class TI, class TO> void gemm32(Sys& s, const GemmP<TI>& q, TO* C, flo
   p.M = q.M; p.N = q.N; p.K = q.K; p.ta = q.ta; p.tb = q.tb; p.tri_a = q.tri_a; p.tri_b = q.tri_b;
   p.c_lower = q.c_lower; p.alpha = alpha; p.beta = beta; p.A = q.A; p.lda = q.lda; p.B = q.B;
   p.ldb = q.ldb; p.C = C; p.ldc = q.ldc;
+  // tile shape: thin products (N or M <= 64) use a 64-wide tile so no half of it idles
+  const int shape = (p.N <= 64 && p.M > 64) ? 1 : ((p.M <= 64 && p.N > 64) ? 2 : 0);
+  const int BM = shape == 2 ? 64 : 128, BN = shape == 1 ? 64 : 128;
   dim3 grid(cdiv(p.M, BM), cdiv(p.N, BN), 1);
   long long tiles = (long long)grid.x * grid.y;
   if (p.c_lower) tiles = (tiles + grid.x) / 2;
@@ -186,7 +206,9 @@ template <class TI, class TO> void gemm32(Sys& s, const GemmP<TI>& q, TO* C, flo
     }
   }
   GEV_COUNT(s);
-  gemm32_kernel<TI, TO><<<grid, NT, 0, s.stream>>>(p);
+  if (shape == 1) gemm32_kernel<TI, TO, 128, 64><<<grid, 128, 0, s.stream>>>(p);
+  else if (shape == 2) gemm32_kernel<TI, TO, 64, 128><<<grid, 128, 0, s.stream>>>(p);
+  else gemm32_kernel<TI, TO, 128, 128><<<grid, 256, 0, s.stream>>>(p);
   if (p.ksplit > 1) {
     unsigned blocks = cdiv((long long)p.M * p.N, 256);
     if (blocks > 8u * s.sms) blocks = 8u * s.sms;

@@ -13,7 +13,8 @@ import pytest
 
 pytestmark = pytest.mark.gpu
 
-SHAPES = [(1, 1, 1), (128, 128, 64), (200, 130, 300), (257, 513, 1000), (1024, 768, 2048), (96, 100, 5000)]
+SHAPES = [(1, 1, 1), (128, 128, 64), (200, 130, 300), (257, 513, 1000), (1024, 768, 2048), (96, 100, 5000),
+          (700, 64, 3000), (50, 700, 2000), (300, 33, 700)]
 
 
 @pytest.fixture(scope="module")
