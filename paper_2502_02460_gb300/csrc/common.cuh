@@ -208,6 +208,7 @@ struct Sys {
   void* splitws = nullptr;  // split-K partials
   size_t splitws_bytes = 0;
   void* band = nullptr;   // compact band, ldband x n
+  void* bandtmp = nullptr;  // complex mixed form: FP64 copy of the band during its conversion
   int ldband = 0;
   void* V2 = nullptr;     // bulge-chasing reflectors, b x (n * ntask)
   void* tau2 = nullptr;   // (n * ntask)

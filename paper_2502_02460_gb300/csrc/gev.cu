@@ -71,6 +71,8 @@ size_t carve(Sys& s, char* base) {
   const bool mixed = s.opts.prec == GEV_MIXED;
   size_t oR1 = L.add(mixed ? n * n * es : 8), oR2 = L.add(mixed ? n * n * es : 8), oR3 = L.add(mixed ? n * n * es : 8);
   size_t oR4 = L.add(mixed && s.dtype == GEV_C128 ? 3 * n * n * es : 8);
+  // complex mixed form: staging copy of the FP64 band while it is converted to complex64
+  size_t obt = L.add(mixed && s.dtype == GEV_C128 ? (size_t)ldband * (n + 2 * b) * es : 8);
   if (base) {
     s.A = base + oA; s.X = base + oX; s.W1 = base + oW1; s.V1 = base + oV1; s.T1 = base + oT1;
     s.dinv = base + odinv; s.Pn = base + oPn; s.small = base + osmall;
@@ -91,6 +93,7 @@ size_t carve(Sys& s, char* base) {
     s.R2 = (double*)(base + oR2);
     s.R3 = (double*)(base + oR3);
     s.R4 = (double*)(base + oR4);
+    s.bandtmp = base + obt;
   }
   return L.total;
 }

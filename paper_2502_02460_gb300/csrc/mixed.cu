@@ -526,7 +526,7 @@ int solve_mixed_cx(Sys& s, const zd* H, int ldh, const zd* S, int lds, int k, do
   mark(GEV_STEP_TO_TRIDIAG);
   {
     const long long bl = (long long)s.ldband * (n + 2 * s.b);
-    zd* tmp = (zd*)s.Q2;  // n^2 doubles >= the band
+    zd* tmp = (zd*)s.bandtmp;  // a copy of the FP64 band, sized like it
     GEV_TRY(copy2d<zd>(s, (int)bl, 1, (const zd*)s.band, bl, tmp, bl));
     GEV_TRY((convert2d<zd, zf>(s, (int)bl, 1, tmp, bl, (zf*)s.band, bl)));
   }
