@@ -58,6 +58,8 @@ def lib() -> ctypes.CDLL:
             getattr(_lib, f"oracle_{p}_check").argtypes = [i, i, dp, i, dp, i, dp, dp, i, dp, dp]
             getattr(_lib, f"oracle_{p}_gev").argtypes = [i, dp, i, dp, i, i, dp, dp, i, dp]
             getattr(_lib, f"oracle_{p}_gev").restype = i
+            getattr(_lib, f"oracle_{p}_density").argtypes = [i, i, dp, i, dp, dp, i]
+            getattr(_lib, f"oracle_{p}_density").restype = None
         _lib.oracle_d_steql.argtypes = [i, dp, dp, dp, dp, i]
         _lib.oracle_d_steql.restype = i
     return _lib
@@ -150,6 +152,18 @@ def normalize_phase(C: np.ndarray) -> np.ndarray:
     n, k = C.shape
     getattr(lib(), f"oracle_{_prefix(C)}_normalize_phase")(n, k, _ptr(C), n)
     return C
+
+
+def density(C: np.ndarray, g: np.ndarray) -> np.ndarray:
+    """Full n x n P with P_ij = sum_l g_l conj(C_il) C_jl (section "Circumventing the eigenvalue
+    problem"; g = occupation numbers f, or f * lambda for the energy-weighted matrix)."""
+    cx = np.iscomplexobj(C)
+    C = _fortran(C, cx)
+    n, k = C.shape
+    g = np.ascontiguousarray(np.broadcast_to(np.asarray(g, dtype=np.float64), (k,)))
+    P = np.zeros((n, n), dtype=C.dtype, order="F")
+    getattr(lib(), f"oracle_{_prefix(C)}_density")(n, k, _ptr(C), n, _ptr(g), _ptr(P), n)
+    return P
 
 
 def gev(H: np.ndarray, S: np.ndarray, k: int):

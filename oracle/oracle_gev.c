@@ -430,6 +430,25 @@ out:
   return status;
 }
 
+/* ---------------------------------------------------------------------------------------------
+ * Density matrix of the computed orbitals (section "Circumventing the eigenvalue problem"):
+ *   P_ij = sum_l  g_l conj(c_li) c_lj,
+ * with c_li = C(i, l) the coefficient of basis function i in orbital l (column l of C).  The weights
+ * g_l are the occupation numbers f_l for the density matrix, or f_l * lambda_l for its
+ * energy-weighted counterpart (section "ELSI").  The plain definition: every entry of the full n x n
+ * P is the sum over l, taken in increasing l.
+ * ------------------------------------------------------------------------------------------- */
+void FN(density)(int n, int k, const scalar* C, int ldc, const double* g, scalar* P, int ldp) {
+#pragma omp parallel for schedule(static)
+  for (int j = 0; j < n; ++j) {
+    for (int i = 0; i < n; ++i) {
+      scalar s = 0;
+      for (int l = 0; l < k; ++l) s += g[l] * CONJ(AT(C, ldc, i, l)) * AT(C, ldc, j, l);
+      AT(P, ldp, i, j) = s;
+    }
+  }
+}
+
 #ifndef ORACLE_COMPLEX
 /* The tridiagonal solver alone (real): eigenvalues ascending into w (length n) and the
    corresponding orthonormal eigenvectors into Z (n x n, ldz).  Returns 0 or -1 (no convergence). */

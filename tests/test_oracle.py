@@ -308,3 +308,60 @@ def test_oracle_thread_count_invariance():
             subprocess.check_call([sys.executable, "-c", code, src, f], env=env, cwd=root)
             outs.append(np.load(f))
     assert np.array_equal(outs[0], outs[1])
+
+
+# ------------------------------------------------------------------------------------ density --
+def _occupied_problem(cx, n=40, k=12, seed=11):
+    p = inputs.make_problem(n, k, seed=seed, complex_=cx)
+    w, C, info, _ = oracle.gev(p.H, p.S, k)
+    assert info == 0
+    return p, w, C
+
+
+@pytest.mark.parametrize("cx", [False, True])
+def test_density_electron_count_and_band_energy(cx):
+    """The density integrates to the electron count and to the band energy: with
+    S_ij = <phi_i|phi_j>, sum_ij P_ij S_ij = sum_l f_l and sum_ij P_ij H_ij = sum_l f_l lambda_l
+    (S-orthonormal orbitals, H c_l = lambda_l S c_l).  For complex data a conjugate on the wrong index
+    breaks both (S is not real), as does a dropped weight or a transposed operand."""
+    p, w, C = _occupied_problem(cx)
+    f = np.random.default_rng(5).uniform(0.0, 2.0, w.size)
+    P = oracle.density(C, f)
+    PE = oracle.density(C, f * w)
+    h1 = norm1(p.H)
+    assert abs(np.sum(P * p.S) - f.sum()) <= 1e-12 * f.sum()
+    assert abs(np.sum(P * p.H) - np.dot(f, w)) <= 1e-12 * h1 * f.sum()
+    assert abs(np.sum(PE * p.S) - np.dot(f, w)) <= 1e-12 * h1 * f.sum()
+    assert np.max(np.abs(P - P.conj().T)) <= 1e-15 * np.max(np.abs(P))
+    if cx:  # the conjugate on the second index instead gives a different number
+        assert abs(np.sum(P.conj() * p.S) - f.sum()) > 1e-6
+
+
+@pytest.mark.parametrize("cx", [False, True])
+def test_density_full_occupation_is_inverse_overlap(cx):
+    """k = n, f = 1: C C^H = S^{-1} for square S-orthonormal C, so P = conj(S^{-1}) (numpy's inverse
+    as the library cross-check)."""
+    n = 24
+    p = inputs.make_problem(n, n, seed=4, complex_=cx)
+    w, C, info, _ = oracle.gev(p.H, p.S, n)
+    assert info == 0
+    P = oracle.density(C, np.ones(n))
+    Si = np.linalg.inv(p.S)
+    assert np.max(np.abs(P - Si.conj())) <= 1e-12 * np.max(np.abs(Si))
+
+
+@pytest.mark.parametrize("cx", [False, True])
+def test_density_idempotent_and_energy_weighted_projection(cx):
+    """f in {0, 1}: P conj(S) P = P (McWeeny idempotency in the non-orthogonal basis) and
+    PE = P conj(H) P (C^H H C = Lambda on the occupied block)."""
+    p, w, C = _occupied_problem(cx, n=36, k=14, seed=8)
+    f = np.zeros(w.size)
+    f[:9] = 1.0
+    P = oracle.density(C, f)
+    PE = oracle.density(C, f * w)
+    scale = np.max(np.abs(P))
+    assert np.max(np.abs(P @ p.S.conj() @ P - P)) <= 1e-12 * scale * norm1(p.S)
+    assert np.max(np.abs(P @ p.H.conj() @ P - PE)) <= 1e-12 * scale * norm1(p.H)
+    # zero occupation: exactly zero
+    assert not np.any(oracle.density(C, np.zeros(w.size)))
+
