@@ -199,6 +199,35 @@ def run_stream(args, dev, mixed=False):
     return st
 
 
+def time_density(solver, Cb, w, Sb, dev, stream, reps=5, warmup=3):
+    """Density matrix and energy-weighted density matrix (gev_density) of the benchmarked orbitals,
+    every orbital doubly occupied; CUDA events on the solver's stream around ``reps`` calls."""
+    import torch
+
+    k, n = Cb.shape
+    occ = torch.full((k,), 2.0, dtype=torch.float64, device=dev)
+    P = solver._empty(n, n)
+    PE = solver._empty(n, n)
+    for _ in range(warmup):
+        solver.density(Cb, occ, w, P=P, PE=PE)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        solver.density(Cb, occ, w, P=P, PE=PE)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    # electron count: sum_ij P_ij S_ij = sum_l f_l (S-orthonormal orbitals)
+    ne = float(torch.sum(P * Sb).real.item())
+    flops = 2 * (n * (n + 1) // 2) * k * (8 if solver.complex else 2)  # P and PE, lower triangles
+    del P, PE
+    return {"ms_per_call": ms, "matrices": 2, "reps": reps, "warmup": warmup,
+            "fp64_tflops": flops / (ms * 1e-3) / 1e12,
+            "electron_count_rel_err": abs(ne - 2.0 * k) / (2.0 * k)}
+
+
 def workload_config(args):
     return {"workload": f"{'complex128' if args.complex else 'real'} N={args.n}, k={args.k} lowest "
                         f"eigenpairs, seed {args.seed}, Toeplitz S, DFT-like spectrum; "
@@ -234,6 +263,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-density", action="store_true",
+                    help="skip timing the density-matrix output of the benchmarked orbitals")
     ap.add_argument("--gen", default="auto", choices=["auto", "cpu", "gpu"],
                     help="where the synthetic pencil is built (auto: GPU for N > 4096)")
     args = ap.parse_args()
@@ -370,6 +401,7 @@ def main():
         e2e = {"value": t_e2e, "unit": "s", "h2d_bytes_per_step": 2 * args.n * args.n * es,
                "d2h_bytes_per_step": args.k * 8 + args.n * args.k * es}
         del Hd, Sd
+    dens = None if args.no_density else time_density(solver, Cb, w, Sb, dev, stream)
     if rank != 0:
         if ws > 1:
             torch.distributed.barrier()
@@ -395,6 +427,7 @@ def main():
         if args.mixed else None,
         "stream": stream_stats,
         "stream_mixed": stream_mixed,
+        "density": dens,
         "roofline": {"bound": "tensor", "kernel": roof_kernel,
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": None,

@@ -124,6 +124,24 @@ int gev_setup(gev_sys** out, int n, int dtype, const gev_opts* opts);
 int gev_solve(gev_sys* s, const void* H, int ldh, const void* S, int lds, int k, double* evals,
               void* C, int ldc, gev_report* rep);
 
+/* Density matrix of k orbitals (section "Circumventing the eigenvalue problem") and, optionally,
+   its energy-weighted counterpart (section "ELSI"):
+       P_ij  = sum_l f_l conj(C_il) C_jl,      PE_ij = sum_l f_l lambda_l conj(C_il) C_jl,
+   C_il being the coefficient of basis function i in orbital l (column l of C, as gev_solve returns).
+   k      : 1 <= k <= n columns of C are used.
+   C      : device, n x k, ldc >= n.
+   occ    : device, k doubles f_l (occupation numbers; any real values).
+   evals  : device, k doubles lambda_l; read only when PE != NULL (may be NULL otherwise).
+   P      : device, n x n, ldp >= n; receives the full Hermitian P (both triangles, real diagonal).
+   PE     : device n x n with ldpe >= n, or NULL; must not be P.
+   C, occ and evals are not modified and must not overlap P or PE.  The products run on the FP64
+   matrix-product engine of the handle (opts.fp64_emulation), also on a GEV_MIXED handle.  Uses the
+   handle's scratch workspace only: the resident factor and the data kept by the step entry points
+   stay valid.  Returns 0, -i for an invalid i-th argument, GEV_ERR_TIMEOUT or GEV_ERR_CUDA.
+   Synchronises the handle's stream before returning. */
+int gev_density(gev_sys* s, int k, const void* C, int ldc, const double* occ, const double* evals, void* P,
+                int ldp, void* PE, int ldpe);
+
 /* enable != 0: keep L^{-1} resident after each solve so the next gev_solve may pass S = NULL
    (SCF iterations with fixed overlap).  enable == 0 drops the resident factor. */
 int gev_reuse_factor(gev_sys* s, int enable);

@@ -319,6 +319,10 @@ int stedc(Sys& s, const double* d, const double* e, int k, double* w, double* Z,
 template <class T> int back(Sys& s, const double* Z, int ldz, int k, T* Y, int ldy);
 template <class T> int bt_he2hb(Sys& s, T* Y, int ldy, int k);
 template <class T> int bt_hb2st(Sys& s, const double* Z, int ldz, int k, T* Y, int ldy);
+// P (and PE when non-null) = sum_l g_l conj(C_il) C_jl, g = occ (and occ * evals), both triangles
+template <class T>
+int density(Sys& s, int k, const T* C, int ldc, const double* occ, const double* evals, T* P, int ldp, T* PE,
+            int ldpe);
 
 // element-wise helpers (kernels in util.cu)
 template <class T> int copy_lower(Sys& s, int n, const T* S, int lds, T* A, int lda);   // A = tril(S), upper 0

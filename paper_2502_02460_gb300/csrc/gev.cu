@@ -261,6 +261,32 @@ int gev_solve(gev_sys* h, const void* H, int ldh, const void* S, int lds, int k,
   return r;
 }
 
+int gev_density(gev_sys* h, int k, const void* C, int ldc, const double* occ, const double* evals, void* P,
+                int ldp, void* PE, int ldpe) {
+  if (!h) return -1;
+  Sys& s = h->s;
+  const int n = s.n;
+  if (k < 1 || k > n) return -2;
+  if (!C) return -3;
+  if (ldc < n) return -4;
+  if (!occ) return -5;
+  if (PE && !evals) return -6;
+  if (!P) return -7;
+  if (ldp < n) return -8;
+  if (PE == P) return -9;
+  if (PE && ldpe < n) return -10;
+  if (cudaSetDevice(s.opts.device) != cudaSuccess) return GEV_ERR_CUDA;
+  s.account = false;
+  GEV_CUDA_TRY(cudaMemsetAsync(s.status, 0, sizeof(int) * ST_COUNT, s.stream));
+  int r = s.dtype == GEV_C128
+              ? density<zd>(s, k, (const zd*)C, ldc, occ, evals, (zd*)P, ldp, (zd*)PE, ldpe)
+              : density<double>(s, k, (const double*)C, ldc, occ, evals, (double*)P, ldp, (double*)PE, ldpe);
+  if (r) return r;
+  GEV_TRY(sync_status(s));
+  if (s.status_h[ST_TIMEOUT]) return GEV_ERR_TIMEOUT;
+  return 0;
+}
+
 // ------------------------------------------------------------------------------ step entries --
 #define STEP_PROLOGUE(h)                                            \
   if (!h) return -1;                                                \

@@ -32,6 +32,7 @@ SYMBOLS = [
     "gev_default_opts", "gev_setup", "gev_solve", "gev_reuse_factor", "gev_free",
     "gev_workspace_bytes", "gev_strerror", "gev_step_potrf", "gev_step_trtri", "gev_step_hegst",
     "gev_step_he2hb", "gev_step_hb2st", "gev_step_stedc", "gev_step_back", "gev_step_mult",
+    "gev_density",
 ]
 
 
@@ -98,6 +99,7 @@ def lib() -> ctypes.CDLL:
         L.gev_step_stedc.argtypes = [vp, vp, vp, i, vp, vp, i, ip]
         L.gev_step_back.argtypes = [vp, vp, i, i, vp, i]
         L.gev_step_mult.argtypes = [vp, vp, i, vp, i, i, vp, i]
+        L.gev_density.argtypes = [vp, i, vp, i, vp, vp, vp, i, vp, i]
         for s in SYMBOLS:
             getattr(L, s).restype = getattr(L, s).restype or ctypes.c_int
         _lib = L
@@ -224,6 +226,31 @@ class Solver:
         Sb = cm(S.to(self.device, self.dtype)) if S is not None else None
         w, Cb = self.solve_cm(Hb, Sb, k)
         return w, logical(Cb)
+
+    def density(self, Cb, occ, evals=None, P=None, PE=None):
+        """Density matrix P_ij = sum_l f_l conj(C_il) C_jl of the columns of C (column-major buffer,
+        n x k) with occupations ``occ`` (device, k doubles); with ``evals`` also the energy-weighted
+        PE (weights f_l lambda_l).  Returns P, or (P, PE): column-major n x n buffers."""
+        import torch
+
+        n = self.n
+        k = Cb.shape[0]
+        if Cb.shape[1] != n or not Cb.is_contiguous():
+            raise ValueError("C must be a contiguous column-major n x k buffer")
+        if P is None:
+            P = self._empty(n, n)
+        if evals is not None and PE is None:
+            PE = self._empty(n, n)
+        occ = occ.to(self.device, torch.float64).contiguous()
+        ev = evals.to(self.device, torch.float64).contiguous() if evals is not None else None
+        if occ.numel() < k or (ev is not None and ev.numel() < k):
+            raise ValueError("occ and evals need k entries")
+        for M in (P, PE):
+            if M is not None and (tuple(M.shape) != (n, n) or not M.is_contiguous() or M.dtype != self.dtype):
+                raise ValueError("P and PE must be contiguous n x n buffers of the handle's dtype")
+        _check(lib().gev_density(self.h, k, _ptr(Cb), n, _ptr(occ), _ptr(ev), _ptr(P), n, _ptr(PE), n),
+               "gev_density")
+        return P if evals is None else (P, PE)
 
     # individual steps (include/gev_steps.h) --------------------------------------------------
     def potrf(self, Ab):
