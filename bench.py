@@ -105,6 +105,30 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def cpu_model() -> str:
+    """Host CPU description for the baseline record: the kernel's model name, else the architecture
+    with its CPU part / implementer codes."""
+    import platform
+
+    name, part, impl = None, None, None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key, _, val = line.partition(":")
+                key, val = key.strip(), val.strip()
+                if key == "model name" and not name:
+                    name = val
+                elif key == "CPU part" and not part:
+                    part = val
+                elif key == "CPU implementer" and not impl:
+                    impl = val
+    except OSError:
+        pass
+    if name:
+        return name
+    return f"{platform.machine()} (implementer {impl}, part {part})" if part else platform.machine()
+
+
 def cpu_baseline(n_full: int, k_full: int, complex_: bool, seconds_target: float = 15.0):
     """The FP64 CPU oracle, as it stands, on a bounded sample of the same recipe, scaled to the
     metric's unit (seconds per N=n_full solve) by the cubic cost of the dense solve."""
@@ -127,7 +151,7 @@ def cpu_baseline(n_full: int, k_full: int, complex_: bool, seconds_target: float
         ns *= 2
     scaled = t * (n_full / ns) ** 3
     return {"value": scaled, "unit": "s", "cores": int(os.environ.get("OMP_NUM_THREADS", cores)),
-            "kind": "oracle",
+            "kind": "oracle", "cpu": cpu_model(),
             "sample": f"oracle on N={ns}, k={max(1, ns * k_full // n_full)} of the same recipe "
                       f"({t:.2f} s), scaled by (N/{ns})^3 to N={n_full}"}
 
@@ -149,7 +173,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(args),
-            "cpu_baseline": {"kind": "oracle", "cores": cores, "sample": sample, "value": v, "unit": "s"},
+            "cpu_baseline": {"kind": "oracle", "cores": cores, "cpu": cpu_model(), "sample": sample, "value": v,
+                             "unit": "s"},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
