@@ -35,8 +35,12 @@ def jacobi_eig(A, tol=1e-15, max_sweeps=100):
             for q in range(p + 1, n):
                 if A[p, q] == 0.0:
                     continue
-                theta = (A[q, q] - A[p, p]) / (2.0 * A[p, q])
-                t = np.sign(theta) / (abs(theta) + np.sqrt(theta * theta + 1.0)) if theta != 0 else 1.0
+                d = A[q, q] - A[p, p]
+                if abs(A[p, q]) <= 1e-150 * abs(d):  # theta would overflow: t = 1/(2 theta) = a_pq/d
+                    t = A[p, q] / d
+                else:
+                    theta = d / (2.0 * A[p, q])
+                    t = np.sign(theta) / (abs(theta) + np.hypot(theta, 1.0)) if theta != 0 else 1.0
                 c = 1.0 / np.sqrt(t * t + 1.0)
                 s = t * c
                 R = np.eye(n)

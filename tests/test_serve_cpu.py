@@ -141,9 +141,9 @@ def _replica(rank, world, out):
 def test_stream_splits_over_two_replicas():
     import torch.multiprocessing as mp
 
-    mgr = mp.Manager()
-    out = mgr.dict()
     ctx = mp.get_context("spawn")
+    mgr = ctx.Manager()
+    out = mgr.dict()
     procs = [ctx.Process(target=_replica, args=(r, 2, out)) for r in range(2)]
     for p in procs:
         p.start()
