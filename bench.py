@@ -37,6 +37,61 @@ METRIC = "N=16384 gen. eigensolve s (FP64 vs mixed, resid≤1e-11); k-pt stream 
 FP64_NOMINAL_TF = 1.25      # GB300 FP64 (DMMA) nominal, dense
 BF16_NOMINAL_TF = 2250.0    # GB300 BF16 nominal, dense
 EMU_PAIRS = 36              # BF16 digit-pair products per emulated FP64 product (p + q <= 9, 8 planes)
+FP64_FMA_TF = 1.00          # GB300 FP64 FMA pipe of the CUDA cores, measured (probe kernel)
+FP32_FMA_TF = 73.9          # GB300 FP32 FMA pipe of the CUDA cores, measured (probe kernel)
+
+
+def steps_roofline(step_ms, n, k, b, complex_, mixed, emulated, refine_iters, fp32_products, mp):
+    """Per-step rates: each step's algorithmic flops (real counts, x4 for complex data) over its
+    measured CUDA-event time, against the peak of the engine that runs the step's arithmetic.
+
+    Peaks: FP64 products emulated on the BF16 tensor cores count 36 BF16 digit-pair products per FP64
+    product (FP64-equivalent peak = BF16 sustained / 36); FP32 products as BF16x6 (x3) split products
+    count 6 (3) BF16 products; native FP64 products run at the BF16 sustained rate times the nominal
+    FP64/BF16 ratio; element-wise FMA work on the CUDA cores uses the measured FMA-pipe rates.  The
+    divide-and-conquer step has no fixed flop count (deflation decides it) and reports its time only;
+    the refinement counts its FP64 work only."""
+    F = 4.0 if complex_ else 1.0
+    N, K, B = float(n), float(k), float(b)
+    bf16 = float(mp.get("bf16_tflops_sustained", 1764.7))
+    if emulated:
+        fp64 = ("FP64 products emulated on BF16 tcgen05 (36 digit-pair MMAs each)", bf16 / EMU_PAIRS)
+    else:
+        fp64 = ("FP64 products on DMMA (mma.sync m8n8k4)", bf16 * FP64_NOMINAL_TF / BF16_NOMINAL_TF)
+    if fp32_products == 0:
+        fp32 = ("FP32 products on the CUDA cores", FP32_FMA_TF)
+    elif fp32_products == 3:
+        fp32 = ("FP32 products as BF16x3 on tcgen05 (thin ones on the CUDA cores)", bf16 / 3)
+    else:
+        fp32 = ("FP32 products as BF16x6 on tcgen05 (thin ones on the CUDA cores)", bf16 / 6)
+    low_real = mixed and not complex_
+    if not mixed:
+        fma = ("FP64 FMA on the CUDA cores", FP64_FMA_TF)
+    else:
+        fma = ("FP32 (complex64) FMA on the CUDA cores", FP32_FMA_TF)
+    work = {
+        "cholesky": (2.0 * N ** 3 / 3.0, fp64),  # Cholesky and inversion, one fused recursion
+        "multiply": (N ** 3, fp64),
+        "to_band": (4.0 * N ** 3 / 3.0, fp32 if low_real else fp64),
+        "to_tridiag": (6.0 * B * N * N, fma),  # bulge chasing: bound by the 3N-task critical path
+        "solve": (None, ("secular equations in FP64 on the CUDA cores; merge products on the product engine",
+                         None)),
+        "back_tridiag": (2.0 * N * N * K, fma),
+        "back_band": (2.0 * N * N * K, fp32 if low_real else fp64),
+        "mult": (N * N * K, fp64),
+    }
+    if mixed:
+        work["refine"] = (refine_iters * (2.0 * N * N * K + 3.0 * N * K * K), fp64)
+    out = {}
+    for step, (flops, (engine, peak)) in work.items():
+        ms = float(step_ms.get(step, 0.0) or 0.0)
+        row = {"ms": ms, "engine": engine}
+        if flops is not None and ms > 0:
+            tf = F * flops / (ms * 1e-3) / 1e12
+            row.update({"flops": F * flops, "tflops": tf, "peak_tflops": peak,
+                        "frac": tf / peak if peak else None})
+        out[step] = row
+    return out
 
 
 def peaks():
@@ -396,6 +451,8 @@ def main():
             out = {"value": f0.elapsed_time(f1) / 1e3, "unit": "s", "steps": 1, "warmup": 1,
                    "fp64_products": "emulated (BF16 digit planes, tcgen05)" if emu else "native (DMMA)",
                    "steps_ms": ps.last_report["ms"],
+                   "steps_roofline": steps_roofline(ps.last_report["ms"], args.n, args.k, args.band_b, args.complex,
+                                                    False, emu != 0, 0, args.fp32_products, mp),
                    "max_abs_eig_err_vs_construction": float(np.max(np.abs(w.cpu().numpy() - p.lam[: args.k])))}
             ps.close()
             return out
@@ -446,6 +503,8 @@ def main():
         "solves_per_s": ws / (ms / 1e3),
         "max_abs_eig_err_vs_construction": err,
         "steps_ms": step_ms,
+        "steps_roofline": steps_roofline(step_ms, args.n, args.k, args.band_b, args.complex, args.mixed, emu_used,
+                                         reps[-1]["refine_iters"] if args.mixed else 0, args.fp32_products, mp),
         "fp64_plain": plain,
         "fp64_plain_emulated_products": plain_emu,
         "refine": {"iterations": reps[-1]["refine_iters"], "residual": reps[-1]["refine_resid"]}
