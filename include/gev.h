@@ -81,7 +81,8 @@ typedef struct {
   int timing;            /* 1: record per-step times into gev_report.ms; 2: also time every GEMM
                             launch (CUDA events) and sum its algorithmic flops (gemm_ms/gemm_flops) */
   int fp64_emulation;    /* FP64 matrix products: 1 = formed from exact BF16 digit planes on the tensor
-                            cores (error below about 2^-50 of the row/column scale; complex data
+                            cores (error below about K 2^-52 times the largest magnitudes of the row of
+                            A and the column of B that meet in an entry; complex data
                             through the real 2x2 embedding), 0 = native FP64 DMMA, -1 = automatic (1) */
   int refine_rr_only;    /* mixed form: 1 = a Rayleigh-Ritz solve in every refinement iteration;
                             0 = Ogita-Aishima steps once the basis is close (default) */

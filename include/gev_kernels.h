@@ -39,7 +39,12 @@ size_t gev_gemm_f32_scratch_bytes(int M, int N, int K);
                      row of op(A) / column of op(B) is scaled by a power of two, split into 8 exact
                      balanced 7-bit digit planes stored as BF16, and the digit products with
                      p + q <= 9 are summed on the tensor cores (exactly, per 512-deep chunk of K, for
-                     p + q <= 7), so the error stays below about 2^-50 (|A| |B|)_ij
+                     p + q <= 7).  The error is bounded relative to the row and column scales:
+                     |err_ij| <= K s_i t_j (2^-52.6 + 2^-53 + K 2^-62.2), s_i (t_j) the power of two
+                     just above the largest magnitude of row i of op(A) (column j of op(B)).  For
+                     entries of similar magnitude this is the order of a native FP64 product's
+                     K 2^-53 (|A| |B|)_ij; entries far below their row's or column's largest keep
+                     fewer bits.
      status_dev    : device pointer to 16 ints (a bounded wait that expired writes status_dev[1])
      scratch_dev   : engine 1: device scratch of scratch_bytes >= gev_gemm_f64_scratch_bytes(M, N, K)
                      (digit planes: about 16 (M + N) min(K, 32768) bytes, plus split-K partials)

@@ -3,8 +3,11 @@ path (engine 0), against an FP64 reference (torch/cuBLAS on the same device).
 
 Bound from the construction: the scaled digits are exact to 2^-55 of the row / column scale, the
 dropped digit pairs are below 2^-55 of it, and every sum is exact except the FP64 epilogue and the
-shared low-order accumulator, so |C - C_ref| <= 4e-15 (|A| |B|)_ij (about 2^-48) for the K used
-here; the same bound holds for the native path.  The shapes cover one and several 512-deep exact
+shared low-order accumulator.  For entries of similar magnitude within each row and column, as
+here (and, with the row scaling, in the wide-range test), that gives |C - C_ref| <= 4e-15
+(|A| |B|)_ij (about 2^-48) for the K used here; the same bound holds for the native path.  The
+general bound, relative to the row and column scales, is checked on a CPU model of the scheme in
+tests/test_fp64_emulation_model.py.  The shapes cover one and several 512-deep exact
 chunks, ragged tiles, split K (few output tiles, long K) and K above one launch's 32768."""
 import ctypes
 
