@@ -4,7 +4,7 @@
 //   x = x1 + x2 + x3 with x1 = bf16(x), x2 = bf16(x - x1), x3 = bf16(x - x1 - x2)  (each step exact
 //   in FP32, so x1 + x2 + x3 carries 24 significant bits: the FP32 value itself)
 //   a b ~ sum over the pairs (p, q) with p + q <= 4 of a_p b_q:
-//     BF16x6: a1b1 + a1b2 + a2b1 + a1b3 + a2b2 + a3b1  (dropped terms below 2^-24 |a b|: FP32 level)
+//     BF16x6: a1b1 + a1b2 + a2b1 + a1b3 + a2b2 + a3b1  (dropped terms at most 2^-23 |a b|: FP32 level)
 //     BF16x3: a1b1 + a1b2 + a2b1                        (about 16 significant bits)
 //   all products of one output accumulate in one FP32 tensor-memory accumulator.
 //
