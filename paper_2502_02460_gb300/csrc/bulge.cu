@@ -457,6 +457,11 @@ template <class T> int hb2st(Sys& s, double* d, double* e) {
     if (G > n - 2) G = n - 2;
     GEV_CUDA_TRY(cudaMemsetAsync(s.prog, 0, sizeof(int) * (size_t)n, s.stream));
     GEV_CUDA_TRY(cudaMemsetAsync(s.tau2, 0, s.es() * (size_t)n * s.ntask, s.stream));
+    // The FP32 back-transform applies every stored slot with its tau (no branch), so the slots of
+    // tasks that never ran (a sweep ends without storing a reflector for its last single row) must
+    // hold zeros, not whatever the workspace held before: 0 * NaN would poison the column.
+    if constexpr (std::is_same<T, float>::value)
+      GEV_CUDA_TRY(cudaMemsetAsync(s.V2, 0, sizeof(T) * (size_t)b * n * s.ntask, s.stream));
     GEV_CUDA_TRY(cudaMemsetAsync(&s.status[ST_ABORT], 0, sizeof(int), s.stream));
     int nn = n, bb = b, lb = ldb, nt = s.ntask;
     T* V2 = (T*)s.V2;
