@@ -89,6 +89,16 @@ typedef struct {
   int fp32_products;     /* mixed form, FP32 matrix products: 6 = BF16x6 split products on the tensor
                             cores (FP32-level accuracy), 3 = BF16x3 (about 16 bits), 0 = FP32 CUDA
                             cores, -1 = automatic (6) */
+  int wait_limit;        /* iteration limit of the bounded waits of the cooperative kernels (the grid
+                            barriers of the full->band panel factorisation, the progress flags of the
+                            bulge chasing; one iteration sleeps ~0.1 us); 0 = default (about 2 s).
+                            A wait that reaches it gives up: the call returns GEV_ERR_TIMEOUT and the
+                            handle stays usable */
+  int check;             /* 1: gev_solve also measures its result on the device, gev_report.resid and
+                            .ortho (two more products of H and S with C: about 4 n^2 k + 2 n k^2 flops);
+                            0 = off (both report -1) */
+  int debug_stall;       /* failure-path tests only: 1 = the bulge chasing waits on a flag that nothing
+                            sets, so its bounded wait expires (GEV_ERR_TIMEOUT); 0 = off */
 } gev_opts;
 
 typedef struct {
@@ -105,6 +115,10 @@ typedef struct {
   double gemm_flops;        /* timing == 2: summed algorithmic GEMM flops (triangles excluded) */
   int refine_oa_steps;      /* mixed form: iterations that took an Ogita-Aishima step in span(Y)
                                instead of the Rayleigh-Ritz solve */
+  double resid;             /* opts.check: ||H C - S C Lambda||_1 / (||H||_1 ||C||_1), computed on the
+                               device from the caller's H and S (the accuracy measure of Eq. 2's
+                               solution); -1 when not computed (opts.check == 0, or S == NULL) */
+  double ortho;             /* opts.check: ||C^H S C - I||_1; -1 when not computed */
 } gev_report;
 
 /* Fill *opts with the defaults (device 0, default stream, GEV_PLAIN, automatic sizes). */
@@ -112,7 +126,10 @@ void gev_default_opts(gev_opts* opts);
 
 /* Create a handle for problems of order n (1 <= n) and the given dtype; allocates the device
    workspace on opts->device.  *out receives the handle (NULL on failure).  opts may be NULL
-   (defaults).  Returns GEV_ERR_OOM when the workspace does not fit (or exceeds workspace_limit). */
+   (defaults).  Returns GEV_ERR_OOM when the workspace does not fit (or exceeds workspace_limit).
+   The handle plays the part of the elsi_handle of the section "Current Status of the
+   Implementation" (ELSI): one per k-point / spin channel, carrying the solver settings, the
+   workspace and the factor of S that later SCF iterations reuse. */
 int gev_setup(gev_sys** out, int n, int dtype, const gev_opts* opts);
 
 /* Solve H C = S C Lambda for the k lowest eigenpairs, 1 <= k <= n.
@@ -143,11 +160,26 @@ int gev_solve(gev_sys* s, const void* H, int ldh, const void* S, int lds, int k,
 int gev_density(gev_sys* s, int k, const void* C, int ldc, const double* occ, const double* evals, void* P,
                 int ldp, void* PE, int ldpe);
 
+/* Accuracy of k eigenpairs (evals, C) of the pencil (H, S), measured on the device with the handle's
+   FP64 product engine: *resid = ||H C - S C Lambda||_1 / (||H||_1 ||C||_1) and
+   *ortho = ||C^H S C - I||_1, the two measures of a solution of Eq. 2 (H C = S C Lambda with
+   S-orthonormal C).  H, S: device, lower triangles read (ldh, lds >= n); evals: device, k doubles;
+   C: device, n x k (ldc >= n); resid, ortho: host.  1 <= k <= n.  Overwrites the handle's scratch
+   workspace (the resident factor stays valid; the reflectors kept by gev_step_he2hb / hb2st do not).
+   Returns 0, -i for an invalid i-th argument, or GEV_ERR_CUDA.  Synchronises the handle's stream. */
+int gev_check(gev_sys* s, const void* H, int ldh, const void* S, int lds, int k, const double* evals,
+              const void* C, int ldc, double* resid, double* ortho);
+
 /* enable != 0: keep L^{-1} resident after each solve so the next gev_solve may pass S = NULL
-   (SCF iterations with fixed overlap).  enable == 0 drops the resident factor. */
+   (SCF iterations with fixed overlap).  enable == 0 drops the resident factor.  Steps 1-2 of the
+   reduction (section "Current Status of the Implementation") depend on S only; the ELSI interface
+   of the same section reuses them across the SCF cycle of one k-point, which this call enables.
+   Returns 0, or -1 for a NULL handle. */
 int gev_reuse_factor(gev_sys* s, int enable);
 
-/* Release the handle and its workspace (s may be NULL). */
+/* Release the handle and its workspace (s may be NULL): the end of an elsi_handle's life (section
+   "Current Status of the Implementation", ELSI).  Synchronises the handle's stream first.
+   Returns 0. */
 int gev_free(gev_sys* s);
 
 /* Device bytes the handle would need for (n, dtype, opts); 0 on invalid arguments. */

@@ -36,12 +36,15 @@ extern "C" {
      info   : optional host pointer; 0, or pivot index + 1 when A is not positive definite (then
               GEV_ERR_NOT_SPD is returned)
    Returns 0, -i for an invalid i-th argument, GEV_ERR_TOO_LARGE, GEV_ERR_NOT_SPD or GEV_ERR_CUDA.
-   The first call on a device looks up the device address of the scratch array
-   (cudaGetSymbolAddress) with that device current; make that first call before any stream
-   capture.  All calls on a device share its one array and each call clears what must start at
+   Set-up: the first call on a device looks up the device address of the scratch array
+   (cudaGetSymbolAddress) with that device current, once; make that first call before any stream
+   capture begins.  Every call synchronises `stream` and copies one status word to the host before
+   it returns.  All calls on a device share its one array and each call clears what must start at
    zero, but nothing else is kept between calls: calls whose work overlaps on the same GPU (issued
    on different streams, or from different host threads) race on the array and must be serialised
-   by the caller.  No cudaMalloc, cudaFree or allocating library routine is called. */
+   by the caller.  The products of this path run on the native FP64 tensor path (DMMA): the
+   emulated FP64 products of a handle need digit-plane workspace that only a handle allocates.
+   No cudaMalloc, cudaFree or allocating library routine is called. */
 int gev_potrf_noalloc(int n, double* A, int lda, void* stream, int* info);
 
 #ifdef __cplusplus

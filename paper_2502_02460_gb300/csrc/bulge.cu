@@ -13,8 +13,9 @@
 // their tasks in order, staging the three blocks of a task (L = (W_t, W_{t-1}), D = (W_t, W_t),
 // E = (W_{t+1}, W_t)) in shared memory; E stays resident as the next task's L.  A per-sweep
 // progress counter (release: __threadfence + store; acquire: volatile load + __threadfence, band
-// reads through L2 with __ldcg) orders the sweeps.  Every wait is bounded (kSpinLimit): on expiry
-// the kernel records ST_TIMEOUT, raises the abort flag and all blocks return.
+// reads through L2 with __ldcg) orders the sweeps.  Every wait is bounded (status[ST_SPIN] iterations
+// when the host set a limit, else kSpinLimit, ~2 s): on expiry the kernel records ST_TIMEOUT, raises
+// the abort flag and all blocks return.
 //
 // The band is stored compactly: element (i, j), 0 <= i-j < 2b, at band[(i-j) + j*ldb], ldb = 2b
 // (rows b+1 .. 2b-1 below the diagonal hold the bulge).
@@ -50,10 +51,11 @@ __device__ bool wait_ge(const int* flag, int target, int* status, int* abort_fla
     int good = 1;
     volatile const int* vf = flag;
     volatile int* va = abort_flag;
+    const long long lim = spin_limit(status);
     long long it = 0;
     while (*vf < target) {
       if (*va) { good = 0; break; }
-      if (++it > kSpinLimit) {
+      if (++it > lim) {
         atomicCAS(&status[ST_TIMEOUT], 0, site);
         atomicExch(abort_flag, 1);
         good = 0;
@@ -87,7 +89,7 @@ __device__ bool wait_ge(const int* flag, int target, int* status, int* abort_fla
 // overlaps the reflector and the update of L.
 template <class T>
 __global__ void __launch_bounds__(NT) k_bulge(int n, int b, T* band, int ldb, T* V2, T* tau2, int ntask,
-                                              int* progress, int* status, int* abort_flag) {
+                                              int* progress, int* status, int* abort_flag, int stall) {
   using R = typename real_of<T>::type;
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int PF = 64 * 64 / NT;  // register prefetch slots per thread (b <= 64)
@@ -113,7 +115,10 @@ __global__ void __launch_bounds__(NT) k_bulge(int n, int b, T* band, int ldb, T*
       const int p = s + 1 + t * b;
       const int len = (p < n) ? min(b, n - p) : 0;
       const int pp = p - b;
-      if (s > 0 && !wait_ge(&progress[s - 1], t + 3, status, abort_flag, 201)) return;
+      // (stall: a failure-path test makes the first wait target a flag that nothing sets)
+      if (s > 0 && !(stall ? wait_ge(&status[ST_STALL], 1, status, abort_flag, 202)
+                           : wait_ge(&progress[s - 1], t + 3, status, abort_flag, 201)))
+        return;
       if (t > 0 && len <= 1) {
         if (pendingL && len == 1)
           for (int q = tid; q < b; q += NT) stcg_(&band[(b - q) + (long long)(pp + q) * ldb], Ls[q * LD]);
@@ -440,11 +445,7 @@ template <class T> int hb2st(Sys& s, double* d, double* e) {
   } else {
     if (b > 64) return GEV_ERR_UNSUPPORTED;
     const size_t smem = bulge_smem<T>(b);
-    static bool attr = false;
-    if (!attr) {
-      GEV_TRY(allow_max_dyn_smem(k_bulge<T>));
-      attr = true;
-    }
+    GEV_TRY(allow_max_dyn_smem(k_bulge<T>));
     int per_sm = 0;
     GEV_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bulge<T>, NT, smem));
     if (per_sm < 1) return GEV_ERR_UNSUPPORTED;
@@ -469,7 +470,8 @@ template <class T> int hb2st(Sys& s, double* d, double* e) {
     int* prog = s.prog;
     int* st = s.status;
     int* ab = &s.status[ST_ABORT];
-    void* args[] = {&nn, &bb, &band, &lb, &V2, &tau2, &nt, &prog, &st, &ab};
+    int stall = s.opts.debug_stall ? 1 : 0;
+    void* args[] = {&nn, &bb, &band, &lb, &V2, &tau2, &nt, &prog, &st, &ab, &stall};
     GEV_COUNT(s);
     GEV_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_bulge<T>, dim3(G), dim3(NT), args, smem, s.stream));
   }
@@ -485,11 +487,7 @@ template <class T, int COLS> int bt_levels(Sys& s, int n, int k, int b, T* Y, in
 template <int B> int bt_levels_f32(Sys& s, int n, int k, float* Y, int ldy) {
   const int ngroups = (n - 3) / B + 1;
   const size_t smem = sizeof(float) * ((size_t)2 * B * (BTF_COLS + 1) + (size_t)B * B + B) + 64;
-  static bool attr = false;
-  if (!attr) {
-    GEV_TRY(allow_max_dyn_smem(k_bt_level_f32<B>));
-    attr = true;
-  }
+  GEV_TRY(allow_max_dyn_smem(k_bt_level_f32<B>));
   const int nlevels = ngroups + s.ntask;
   const unsigned ycb = cdiv(k, BTF_COLS);
   for (int L = 0; L < nlevels; ++L) {
@@ -531,11 +529,7 @@ template <class T, int COLS> int bt_levels(Sys& s, int n, int k, int b, T* Y, in
   const int last_sweep = n - 3;
   const int ngroups = last_sweep / G + 1;
   const size_t smem = sizeof(T) * ((size_t)2 * b * COLS + (size_t)G * b + G) + 64;
-  static bool attr = false;
-  if (!attr) {
-    GEV_TRY(allow_max_dyn_smem(k_bt_bulge_level<T, COLS>));
-    attr = true;
-  }
+  GEV_TRY(allow_max_dyn_smem(k_bt_bulge_level<T, COLS>));
   const int nlevels = ngroups + s.ntask;
   const unsigned ycb = cdiv(k, COLS);
   for (int L = 0; L < nlevels; ++L) {

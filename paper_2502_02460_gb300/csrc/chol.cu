@@ -101,14 +101,8 @@ __global__ void k_inv_diag_blocks(int n, int nb, const T* A, long long lda, T* D
 template <class T> size_t diag_smem() { return sizeof(T) * 2 * NBMAX * LDS; }
 
 template <class T> int set_smem_attrs() {
-  static bool done = false;
-  if (!done) {
-    GEV_CUDA_TRY(cudaFuncSetAttribute(k_potrf_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)diag_smem<T>()));
-    GEV_CUDA_TRY(cudaFuncSetAttribute(k_inv_diag_blocks<T>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)diag_smem<T>()));
-    done = true;
-  }
+  GEV_TRY(allow_dyn_smem(k_potrf_diag<T>, diag_smem<T>()));
+  GEV_TRY(allow_dyn_smem(k_inv_diag_blocks<T>, diag_smem<T>()));
   return 0;
 }
 

@@ -132,11 +132,21 @@ enum StatusSlot {
   ST_BARRIER_GEN = 4,   // grid-barrier generation counter (cooperative kernels)
   ST_BARRIER_CNT = 5,   // grid-barrier arrival counter
   ST_ABORT = 6,         // non-zero once a cooperative kernel gave up waiting
+  ST_CONFIG = 7,        // non-zero: a launch could not be configured (site code); reported as GEV_ERR_CUDA
+  ST_SPIN = 8,          // iteration limit of every bounded device wait (0: kSpinLimit); set by the host
+  ST_STALL = 9,         // a flag nothing ever sets: the bulge chase waits on it when asked to stall
   ST_COUNT = 16
 };
 
 // Bounded spin limit for every device-side wait (iterations of a ~100 ns nanosleep loop).
 constexpr long long kSpinLimit = 20000000;  // ~2 s
+
+// The wait limit of the current launch: status[ST_SPIN] when the host set one (gev_opts.wait_limit),
+// else kSpinLimit.  Read once per wait, through L2.
+__device__ __forceinline__ long long spin_limit(const int* status) {
+  const int v = status ? __ldcg(&status[ST_SPIN]) : 0;
+  return v > 0 ? (long long)v : kSpinLimit;
+}
 
 // -------------------------------------------------------------------------------------- GEMM --
 // C[M x N] = alpha op(A) op(B) + beta C, column-major.
@@ -243,6 +253,7 @@ struct Sys {
   int ev_step[2 * GEV_NSTEPS + 2] = {};  // step id of each recorded mark (-1: end)
   int n_marks = 0;
   int* status_h = nullptr;  // pinned host mirror
+  int spin_h = 0;           // host copy of the wait limit written to status[ST_SPIN]
 
   // accounting of the current call
   long long launches = 0;
@@ -295,17 +306,14 @@ inline void step_collect(Sys& s, double* ms);
 
 inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
 
-// Raise a kernel's dynamic shared-memory limit to what the device allows beside its static use.
-template <class F> int allow_max_dyn_smem(F* func) {
-  int dev = 0, optin = 0;
-  GEV_CUDA_TRY(cudaGetDevice(&dev));
-  GEV_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  cudaFuncAttributes fa{};
-  GEV_CUDA_TRY(cudaFuncGetAttributes(&fa, (const void*)func));
-  GEV_CUDA_TRY(cudaFuncSetAttribute((const void*)func, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    optin - (int)fa.sharedSizeBytes));
-  return 0;
-}
+// Raise a kernel's dynamic shared-memory limit on the CURRENT device, once per (kernel, device).
+// cudaFuncSetAttribute acts on the current device only, and one process may drive several devices
+// (gev_opts.device) from several host threads, so the bookkeeping is per device and under a lock
+// (util.cu).  bytes < 0: the most the device allows beside the kernel's static shared memory.
+// Returns 0 or GEV_ERR_CUDA (the failing call is reported on stderr).
+int set_dyn_smem(const void* func, int bytes);
+template <class F> int allow_max_dyn_smem(F* func) { return set_dyn_smem((const void*)func, -1); }
+template <class F> int allow_dyn_smem(F* func, size_t bytes) { return set_dyn_smem((const void*)func, (int)bytes); }
 
 // ---------------------------------------------------------------------------- step launchers --
 template <class T> int potrf_inv(Sys& s, T* A, int lda);  // S (lower) -> L^{-1}, one recursion
@@ -335,6 +343,17 @@ template <class TA, class TB>
 int convert2d(Sys& s, int m, int n, const TA* src, long long lds, TB* dst, long long ldd);
 template <class T> int normalize_phase(Sys& s, int n, int k, T* C, int ldc);
 int sync_status(Sys& s);  // synchronise the stream, copy the status words to the host mirror
+int reset_status(Sys& s);  // zero the status words (and set the wait limit of opts.wait_limit)
+// After a step with bounded waits: synchronise, and return GEV_ERR_TIMEOUT when a wait gave up (the
+// later steps would only work on the abandoned data).
+inline int stop_on_timeout(Sys& s) {
+  GEV_TRY(sync_status(s));
+  return s.status_h[ST_TIMEOUT] ? GEV_ERR_TIMEOUT : 0;
+}
+// gev_opts.check: residual and orthogonality of a solution, on the device (check.cu)
+template <class T>
+int measure(Sys& s, const T* H, int ldh, const T* S, int lds, int k, const double* evals, const T* C, int ldc,
+            double* resid, double* ortho);
 // mixed form (mixed.cu): FP32 reduction, FP64 Ogita-Aishima refinement of the standard problem
 int solve_mixed(Sys& s, const double* H, int ldh, const double* S, int lds, int k, double* evals,
                 double* C, int ldc, gev_report* rep);

@@ -1,5 +1,6 @@
 // Grid-wide barrier for cooperatively launched kernels (all blocks co-resident), with a bounded
-// wait: a block that waits longer than kSpinLimit iterations sets status[ST_TIMEOUT] and an abort
+// wait: a block that waits longer than the launch's limit (status[ST_SPIN] when the host set one,
+// else kSpinLimit, ~2 s) sets status[ST_TIMEOUT] and an abort
 // flag, and every block then leaves the kernel at its next barrier.  No wait is unbounded.
 #pragma once
 #include "common.cuh"
@@ -30,10 +31,11 @@ __device__ __forceinline__ bool grid_sync(const GridBar& g, int site) {
       __threadfence();
       atomicAdd(g.gen, 1u);
     } else {
+      const long long lim = spin_limit(g.status);
       long long it = 0;
       while (*vgen == my_gen) {
         if (*vab) { ok = 0; break; }
-        if (++it > kSpinLimit) {
+        if (++it > lim) {
           atomicCAS(&g.status[ST_TIMEOUT], 0, site);
           atomicExch(g.abort_flag, 1);
           ok = 0;

@@ -257,8 +257,44 @@ int gev_solve(gev_sys* h, const void* H, int ldh, const void* S, int lds, int k,
     r = solve_mixed(s, (const double*)H, ldh, (const double*)S, lds, k, evals, (double*)C, ldc, rep);
   else
     r = solve_t<double>(s, (const double*)H, ldh, (const double*)S, lds, k, evals, (double*)C, ldc, rep);
-  if (rep) rep->workspace_bytes = s.bytes;
+  if (rep) {
+    rep->workspace_bytes = s.bytes;
+    rep->resid = -1.0;
+    rep->ortho = -1.0;
+  }
+  if (r == 0 && s.opts.check && S && rep) {
+    // the accuracy of the returned pencil solution, on the device (two more products with C)
+    const int rc = s.dtype == GEV_C128
+                       ? measure<zd>(s, (const zd*)H, ldh, (const zd*)S, lds, k, evals, (const zd*)C, ldc,
+                                     &rep->resid, &rep->ortho)
+                       : measure<double>(s, (const double*)H, ldh, (const double*)S, lds, k, evals,
+                                         (const double*)C, ldc, &rep->resid, &rep->ortho);
+    if (rc) return rc;
+  }
   return r;
+}
+
+int gev_check(gev_sys* h, const void* H, int ldh, const void* S, int lds, int k, const double* evals,
+              const void* C, int ldc, double* resid, double* ortho) {
+  if (!h) return -1;
+  Sys& s = h->s;
+  const int n = s.n;
+  if (!H) return -2;
+  if (ldh < n) return -3;
+  if (!S) return -4;
+  if (lds < n) return -5;
+  if (k < 1 || k > n) return -6;
+  if (!evals) return -7;
+  if (!C) return -8;
+  if (ldc < n) return -9;
+  if (!resid) return -10;
+  if (!ortho) return -11;
+  if (cudaSetDevice(s.opts.device) != cudaSuccess) return GEV_ERR_CUDA;
+  GEV_TRY(reset_status(s));
+  return s.dtype == GEV_C128 ? measure<zd>(s, (const zd*)H, ldh, (const zd*)S, lds, k, evals, (const zd*)C, ldc,
+                                           resid, ortho)
+                             : measure<double>(s, (const double*)H, ldh, (const double*)S, lds, k, evals,
+                                               (const double*)C, ldc, resid, ortho);
 }
 
 int gev_density(gev_sys* h, int k, const void* C, int ldc, const double* occ, const double* evals, void* P,
@@ -277,7 +313,7 @@ int gev_density(gev_sys* h, int k, const void* C, int ldc, const double* occ, co
   if (PE && ldpe < n) return -10;
   if (cudaSetDevice(s.opts.device) != cudaSuccess) return GEV_ERR_CUDA;
   s.account = false;
-  GEV_CUDA_TRY(cudaMemsetAsync(s.status, 0, sizeof(int) * ST_COUNT, s.stream));
+  GEV_TRY(reset_status(s));
   int r = s.dtype == GEV_C128
               ? density<zd>(s, k, (const zd*)C, ldc, occ, evals, (zd*)P, ldp, (zd*)PE, ldpe)
               : density<double>(s, k, (const double*)C, ldc, occ, evals, (double*)P, ldp, (double*)PE, ldpe);
@@ -297,7 +333,7 @@ int gev_step_potrf(gev_sys* h, void* A, int lda, int* info) {
   STEP_PROLOGUE(h)
   if (!A) return -2;
   if (lda < s.n) return -3;
-  GEV_CUDA_TRY(cudaMemsetAsync(s.status, 0, sizeof(int) * ST_COUNT, s.stream));
+  GEV_TRY(reset_status(s));
   int r = s.dtype == GEV_C128 ? potrf<zd>(s, (zd*)A, lda) : potrf<double>(s, (double*)A, lda);
   if (r) return r;
   GEV_TRY(sync_status(s));
@@ -350,7 +386,7 @@ int gev_step_hb2st(gev_sys* h, double* d, double* e) {
   if (!d) return -2;
   if (!e && s.n > 1) return -3;
   if (!s.have_band) return GEV_ERR_UNSUPPORTED;
-  GEV_CUDA_TRY(cudaMemsetAsync(s.status, 0, sizeof(int) * ST_COUNT, s.stream));
+  GEV_TRY(reset_status(s));
   int r = s.dtype == GEV_C128 ? hb2st<zd>(s, d, e) : hb2st<double>(s, d, e);
   if (r) return r;
   GEV_TRY(sync_status(s));
@@ -367,7 +403,7 @@ int gev_step_stedc(gev_sys* h, const double* d, const double* e, int k, double* 
   if (!w) return -5;
   if (!Z) return -6;
   if (ldz < s.n) return -7;
-  GEV_CUDA_TRY(cudaMemsetAsync(s.status, 0, sizeof(int) * ST_COUNT, s.stream));
+  GEV_TRY(reset_status(s));
   int r = stedc(s, d, e, k, w, Z, ldz, deflated);
   if (r) return r;
   GEV_TRY(sync_status(s));
@@ -421,7 +457,7 @@ template <class T> int solve_t(Sys& s, const T* H, int ldh, const T* S, int lds,
   s.launches = 0;
   s.gemm_used = 0;
   s.account = s.opts.timing == 2;
-  GEV_CUDA_TRY(cudaMemsetAsync(s.status, 0, sizeof(int) * ST_COUNT, s.stream));
+  GEV_TRY(reset_status(s));
   mark(GEV_STEP_CHOLESKY);
   const bool reuse = (S == nullptr);
   if (!reuse) {
@@ -449,6 +485,7 @@ template <class T> int solve_t(Sys& s, const T* H, int ldh, const T* S, int lds,
   GEV_TRY(he2hb<T>(s, A, n, s.b));
   mark(GEV_STEP_TO_TRIDIAG);
   GEV_TRY(hb2st<T>(s, s.d, s.e));
+  GEV_TRY(stop_on_timeout(s));
   // step 5: divide and conquer, k lowest vectors
   mark(GEV_STEP_SOLVE);
   GEV_TRY(stedc(s, s.d, s.e, k, s.w, s.Zk, n, nullptr));

@@ -286,7 +286,7 @@ int solve_mixed(Sys& s, const double* H, int ldh, const double* S, int lds, int 
   auto mark = [&](int step) { step_mark(s, step); };
   double* A = (double*)s.A;
   double* X = (double*)s.X;
-  GEV_CUDA_TRY(cudaMemsetAsync(s.status, 0, sizeof(int) * ST_COUNT, st));
+  GEV_TRY(reset_status(s));
   // ---- FP64: Cholesky, inversion, Multiply
   mark(GEV_STEP_CHOLESKY);
   const bool reuse = (S == nullptr);
@@ -313,6 +313,7 @@ int solve_mixed(Sys& s, const double* H, int ldh, const double* S, int lds, int 
   GEV_TRY(he2hb<float>(s, A32, n, s.b));
   mark(GEV_STEP_TO_TRIDIAG);
   GEV_TRY(hb2st<float>(s, s.d, s.e));
+  GEV_TRY(stop_on_timeout(s));
   mark(GEV_STEP_SOLVE);
   s.dc_lowp = 1;
   int r = stedc(s, s.d, s.e, n, s.w, s.Zk, n, nullptr);
@@ -362,6 +363,8 @@ int solve_mixed(Sys& s, const double* H, int ldh, const double* S, int lds, int 
     o.workspace_limit = 0;
     o.band_b = 0;
     o.fp64_emulation = s.emu_fp64;  // the Ritz pencil's products use the same FP64 engine
+    o.check = 0;
+    o.debug_stall = 0;
     gev_sys* h = nullptr;
     const int rc = gev_setup(&h, k, GEV_F64, &o);
     if (rc) return rc;
@@ -498,7 +501,7 @@ int solve_mixed_cx(Sys& s, const zd* H, int ldh, const zd* S, int lds, int k, do
   zd* A = (zd*)s.A;
   zd* X = (zd*)s.X;
   const zd one = make_zd(1.0, 0.0), zero = make_zd(0.0, 0.0);
-  GEV_CUDA_TRY(cudaMemsetAsync(s.status, 0, sizeof(int) * ST_COUNT, st));
+  GEV_TRY(reset_status(s));
   mark(GEV_STEP_CHOLESKY);
   const bool reuse = (S == nullptr);
   if (!reuse) {
@@ -531,6 +534,7 @@ int solve_mixed_cx(Sys& s, const zd* H, int ldh, const zd* S, int lds, int k, do
     GEV_TRY((convert2d<zd, zf>(s, (int)bl, 1, tmp, bl, (zf*)s.band, bl)));
   }
   GEV_TRY(hb2st<zf>(s, s.d, s.e));
+  GEV_TRY(stop_on_timeout(s));
   mark(GEV_STEP_SOLVE);
   s.dc_lowp = 1;
   int r = stedc(s, s.d, s.e, n, s.w, s.Zk, n, nullptr);
@@ -580,6 +584,8 @@ int solve_mixed_cx(Sys& s, const zd* H, int ldh, const zd* S, int lds, int k, do
     o.workspace_limit = 0;
     o.band_b = 0;
     o.fp64_emulation = s.emu_fp64;
+    o.check = 0;
+    o.debug_stall = 0;
     gev_sys* h = nullptr;
     const int rc = gev_setup(&h, k, GEV_C128, &o);
     if (rc) return rc;

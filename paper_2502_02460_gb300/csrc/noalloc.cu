@@ -56,7 +56,11 @@ extern "C" int gev_potrf_noalloc(int n, double* A, int lda, void* cuda_stream, i
   GEV_CUDA_TRY(cudaGetDevice(&dev));
   void* base = nullptr;
   GEV_TRY(scratch_address(dev, &base));
-  gev::Sys s;  // a view of the fixed scratch: no workspace of its own
+  // A view of the fixed scratch, no workspace of its own.  A default Sys has emu_fp64 = 0, so every
+  // product of the path runs on the native FP64 tensor path (DMMA): the emulated FP64 products need
+  // digit-plane scratch (ozws) of the size of the operands, which only a handle allocates.  With
+  // splitws empty no product splits K (the panel products have K = nb anyway).
+  gev::Sys s;
   s.n = n;
   s.dtype = GEV_F64;
   s.nb = kNb;

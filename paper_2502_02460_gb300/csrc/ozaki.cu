@@ -556,16 +556,16 @@ namespace {
 // K pieces of one launch; rs = 1 for complex products.
 void emulate(Sys& s, int M, int N, int K, Opnd a, size_t a_kstep, Opnd b, size_t b_kstep, int tri_a, int tri_b,
              int c_lower, int rs, double alpha, double beta, double* C, long long ldc) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute((const void*)ozaki_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_OZ);
-    attr = true;
-  }
   const OzLayout L = oz_layout(M, N, K);
+  int site = 0;
   if (s.ozws == nullptr || L.total > s.ozws_bytes) {  // internal sizing error: fail the call loudly
     fprintf(stderr, "gev: emulated FP64 GEMM scratch too small (%zu < %zu bytes)\n", s.ozws_bytes, L.total);
-    const int site = 499;
-    if (s.status) cudaMemcpyAsync(s.status + ST_TIMEOUT, &site, sizeof(int), cudaMemcpyHostToDevice, s.stream);
+    site = 499;
+  } else if (allow_dyn_smem(ozaki_kernel, SMEM_OZ) != 0) {
+    site = 498;
+  }
+  if (site) {  // recorded in the status words: the caller's next status check returns GEV_ERR_CUDA
+    if (s.status) cudaMemcpyAsync(s.status + ST_CONFIG, &site, sizeof(int), cudaMemcpyHostToDevice, s.stream);
     cudaStreamSynchronize(s.stream);
     return;
   }

@@ -198,11 +198,7 @@ template <class T> size_t panel_smem(int R, int b, int use_smem) {
 
 template <class T> int he2hb(Sys& s, T* A, int lda, int b) {
   const int n = s.n;
-  static bool attr = false;
-  if (!attr) {
-    GEV_TRY(allow_max_dyn_smem(k_panel_qr<T>));
-    attr = true;
-  }
+  GEV_TRY(allow_max_dyn_smem(k_panel_qr<T>));
   T* V1 = (T*)s.V1;
   T* T1 = (T*)s.T1;
   T* W0 = (T*)s.Pn;

@@ -287,11 +287,7 @@ template <class TI, class TO>
 bool gemm_tc32(Sys& s, const GemmP<TI>& q, TO* C, float alpha, float beta, int nprod) {
   if (q.M <= 0 || q.N <= 0) return true;
   if (!s.ozws || gemm_tc32_scratch(q.M, q.N, q.K) > s.ozws_bytes) return false;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute((const void*)tc32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_TC);
-    attr = true;
-  }
+  if (allow_dyn_smem(tc32_kernel, SMEM_TC) != 0) return false;  // the caller takes the CUDA-core product
   const size_t Mp = rup(q.M, TM), Kp = rup(std::max(q.K, 1), KS);
   unsigned char* Ap = static_cast<unsigned char*>(s.ozws);
   unsigned char* Bp = Ap + rup(Mp * Kp * 2 * NPL, 256);

@@ -1,9 +1,44 @@
 // Element-wise helpers of the solver: triangle copies, Hermitian sums and mirrors (32x32 tiles
 // through shared memory, so both the read and the transposed write are coalesced), 2-D copies,
 // and the per-column phase normalisation of the eigenvectors.
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "common.cuh"
 
 namespace gev {
+
+int set_dyn_smem(const void* func, int bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, int> done;  // (kernel, device) -> bytes allowed
+  int dev = 0;
+  GEV_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  const auto key = std::make_pair(func, dev);
+  const auto it = done.find(key);
+  if (it != done.end() && (bytes < 0 || it->second >= bytes)) return 0;
+  int want = bytes;
+  if (want < 0) {
+    int optin = 0;
+    GEV_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa{};
+    GEV_CUDA_TRY(cudaFuncGetAttributes(&fa, func));
+    want = optin - (int)fa.sharedSizeBytes;
+  }
+  GEV_CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, want));
+  done[key] = want;
+  return 0;
+}
+
+int reset_status(Sys& s) {
+  GEV_CUDA_TRY(cudaMemsetAsync(s.status, 0, sizeof(int) * ST_COUNT, s.stream));
+  if (s.opts.wait_limit > 0) {
+    s.spin_h = s.opts.wait_limit;
+    GEV_CUDA_TRY(cudaMemcpyAsync(&s.status[ST_SPIN], &s.spin_h, sizeof(int), cudaMemcpyHostToDevice, s.stream));
+  }
+  return 0;
+}
 
 namespace {
 
@@ -221,6 +256,10 @@ int sync_status(Sys& s) {
   GEV_CUDA_TRY(cudaMemcpyAsync(s.status_h, s.status, sizeof(int) * ST_COUNT, cudaMemcpyDeviceToHost,
                                s.stream));
   GEV_CUDA_TRY(cudaStreamSynchronize(s.stream));
+  if (s.status_h[ST_CONFIG]) {
+    fprintf(stderr, "gev: a launch could not be configured (site %d)\n", s.status_h[ST_CONFIG]);
+    return GEV_ERR_CUDA;
+  }
   return 0;
 }
 

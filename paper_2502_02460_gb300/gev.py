@@ -32,7 +32,7 @@ SYMBOLS = [
     "gev_default_opts", "gev_setup", "gev_solve", "gev_reuse_factor", "gev_free",
     "gev_workspace_bytes", "gev_strerror", "gev_step_potrf", "gev_step_trtri", "gev_step_hegst",
     "gev_step_he2hb", "gev_step_hb2st", "gev_step_stedc", "gev_step_back", "gev_step_mult",
-    "gev_density",
+    "gev_density", "gev_check",
 ]
 
 
@@ -49,7 +49,8 @@ class Opts(ctypes.Structure):
                 ("band_b", ctypes.c_int), ("panel_nb", ctypes.c_int), ("refine_tol", ctypes.c_double),
                 ("refine_max_iter", ctypes.c_int), ("workspace_limit", ctypes.c_size_t),
                 ("timing", ctypes.c_int), ("fp64_emulation", ctypes.c_int),
-                ("refine_rr_only", ctypes.c_int), ("fp32_products", ctypes.c_int)]
+                ("refine_rr_only", ctypes.c_int), ("fp32_products", ctypes.c_int),
+                ("wait_limit", ctypes.c_int), ("check", ctypes.c_int), ("debug_stall", ctypes.c_int)]
 
 
 class Report(ctypes.Structure):
@@ -58,14 +59,15 @@ class Report(ctypes.Structure):
                 ("ms", ctypes.c_double * NSTEPS), ("workspace_bytes", ctypes.c_size_t),
                 ("launches", ctypes.c_longlong), ("gemm_calls", ctypes.c_int),
                 ("gemm_ms", ctypes.c_double), ("gemm_flops", ctypes.c_double),
-                ("refine_oa_steps", ctypes.c_int)]
+                ("refine_oa_steps", ctypes.c_int), ("resid", ctypes.c_double), ("ortho", ctypes.c_double)]
 
     def as_dict(self):
         return {"info": self.info, "deflated": self.deflated, "refine_iters": self.refine_iters,
                 "reused_factor": self.reused_factor, "refine_resid": self.refine_resid,
                 "ms": dict(zip(STEP_NAMES, list(self.ms))), "workspace_bytes": self.workspace_bytes,
                 "launches": self.launches, "gemm_calls": self.gemm_calls, "gemm_ms": self.gemm_ms,
-                "gemm_flops": self.gemm_flops, "refine_oa_steps": self.refine_oa_steps}
+                "gemm_flops": self.gemm_flops, "refine_oa_steps": self.refine_oa_steps,
+                "resid": self.resid, "ortho": self.ortho}
 
 
 _lib = None
@@ -100,6 +102,8 @@ def lib() -> ctypes.CDLL:
         L.gev_step_back.argtypes = [vp, vp, i, i, vp, i]
         L.gev_step_mult.argtypes = [vp, vp, i, vp, i, i, vp, i]
         L.gev_density.argtypes = [vp, i, vp, i, vp, vp, vp, i, vp, i]
+        dpp = ctypes.POINTER(ctypes.c_double)
+        L.gev_check.argtypes = [vp, vp, i, vp, i, i, vp, vp, i, dpp, dpp]
         for s in SYMBOLS:
             getattr(L, s).restype = getattr(L, s).restype or ctypes.c_int
         _lib = L
@@ -145,7 +149,8 @@ class Solver:
     def __init__(self, n: int, complex_: bool = False, device=None, mixed: bool = False,
                  band_b: int = 0, panel_nb: int = 0, timing: int = 0, stream=None,
                  workspace_limit: int = 0, refine_tol: float = 0.0, refine_max_iter: int = 0,
-                 fp64_emulation: int = -1, refine_rr_only: int = 0, fp32_products: int = -1):
+                 fp64_emulation: int = -1, refine_rr_only: int = 0, fp32_products: int = -1,
+                 wait_limit: int = 0, check: bool = False, debug_stall: bool = False):
         import torch
 
         if not torch.cuda.is_available():
@@ -171,6 +176,9 @@ class Solver:
         o.fp64_emulation = fp64_emulation
         o.refine_rr_only = refine_rr_only
         o.fp32_products = fp32_products
+        o.wait_limit = int(wait_limit)
+        o.check = 1 if check else 0
+        o.debug_stall = 1 if debug_stall else 0
         self.opts = o
         h = ctypes.c_void_p()
         _check(lib().gev_setup(ctypes.byref(h), n, GEV_C128 if complex_ else GEV_F64, ctypes.byref(o)),
@@ -251,6 +259,17 @@ class Solver:
         _check(lib().gev_density(self.h, k, _ptr(Cb), n, _ptr(occ), _ptr(ev), _ptr(P), n, _ptr(PE), n),
                "gev_density")
         return P if evals is None else (P, PE)
+
+    def check(self, Hb, Sb, evals, Cb):
+        """(resid, ortho) of the eigenpairs (evals, C) of the pencil (H, S), measured on the device:
+        ||HC - SC Lambda||_1/(||H||_1 ||C||_1) and ||C^H S C - I||_1 (column-major buffers)."""
+        n = self.n
+        k = Cb.shape[0]
+        r = ctypes.c_double(0.0)
+        o = ctypes.c_double(0.0)
+        _check(lib().gev_check(self.h, _ptr(Hb), n, _ptr(Sb), n, k, _ptr(evals), _ptr(Cb), n,
+                               ctypes.byref(r), ctypes.byref(o)), "gev_check")
+        return r.value, o.value
 
     # individual steps (include/gev_steps.h) --------------------------------------------------
     def potrf(self, Ab):

@@ -9,6 +9,7 @@ import pytest
 
 import oracle
 from paper_2502_02460_gb300 import inputs
+from tests.parity import compare_to_oracle
 from tests.pins import norm1
 
 pytestmark = pytest.mark.gpu
@@ -98,6 +99,9 @@ def test_mixed_complex_matches_oracle(dev, n, k, cluster):
     assert r <= 1e-11, r
     assert o <= 1e-12 * np.sqrt(n), o
     assert rep["refine_iters"] <= 5 and rep["refine_resid"] <= 1e-11
+    # each vector against the oracle's (phase free): |c^H S c_oracle| = 1 for separated eigenvalues,
+    # the overlap block's singular values = 1 inside the cluster
+    compare_to_oracle(p, w, C, k, resid_bound=1e-11, ref=(wo, Co, info, None))
 
 
 @pytest.mark.parametrize("n,k,cluster", [(1500, 400, False), (1200, 300, True)])

@@ -11,6 +11,7 @@ import pytest
 
 import oracle
 from paper_2502_02460_gb300 import inputs
+from tests.parity import compare_to_oracle
 from tests.pins import norm1, sturm_count
 
 pytestmark = pytest.mark.gpu
@@ -134,33 +135,6 @@ def test_standard_problem_chain(dev, cx, n, k, b):
 
 
 # ------------------------------------------------------------------------------- whole solve --
-def compare_to_oracle(p, w, C, k, tol_vec=1e-8):
-    wo, Co, info, dg = oracle.gev(p.H, p.S, k)
-    assert info == 0
-    h1 = norm1(p.H)
-    n = p.n
-    assert np.max(np.abs(w - wo)) <= 1e-11 * h1
-    assert np.max(np.abs(w - p.lam[:k])) <= 1e-11 * h1
-    r, o = oracle.check(p.H, p.S, w, C)
-    assert r <= 1e-13 * np.sqrt(n), r
-    assert o <= 1e-12 * np.sqrt(n), o
-    # eigenvectors: clusters by eigenvalue proximity
-    G = Co.conj().T @ (p.S @ C)  # k x k overlaps
-    groups = []
-    start = 0
-    for i in range(1, k + 1):
-        if i == k or wo[i] - wo[i - 1] > 1e-6 * h1:
-            groups.append((start, i))
-            start = i
-    for a, bnd in groups:
-        if bnd - a == 1:
-            assert abs(abs(G[a, a]) - 1.0) <= tol_vec
-        else:
-            blk = G[a:bnd, a:bnd]
-            sv = np.linalg.svd(blk, compute_uv=False)
-            assert np.max(np.abs(sv - 1.0)) <= 1e-6
-
-
 @pytest.mark.parametrize("cx", [False, True])
 @pytest.mark.parametrize("n,k", [(1, 1), (2, 2), (3, 1), (64, 64), (100, 33), (200, 200), (333, 100)])
 def test_solve_matches_oracle(dev, cx, n, k):
