@@ -19,6 +19,7 @@
 //
 // The band is stored compactly: element (i, j), 0 <= i-j < 2b, at band[(i-j) + j*ldb], ldb = 2b
 // (rows b+1 .. 2b-1 below the diagonal hold the bulge).
+#include <algorithm>
 #include <climits>
 
 #include <type_traits>
@@ -432,6 +433,69 @@ __global__ void __launch_bounds__(BTF_COLS) k_bt_level_f32(int n, int k, int L, 
   }
 }
 
+// Compact-WY form of one level's reflector blocks, for the tensor-core back-transform: for block j
+// (group g = g_lo + j, task t) with reflectors v_q = V(:, q) of sweeps s0 + q on the window rows
+// [w0, w0 + 2b) (v_q non-zero in rows q .. q + b - 1, v_q(q) = 1),
+//   D_j = H(s0) H(s0 + 1) ... H(s0 + b - 1) = I - V T V^H,  T upper triangular:
+//   T_qq = tau_q,  T(0:q, q) = -tau_q T(0:q, 0:q) (V(:, 0:q)^H v_q),
+// and W_j = V T (2b x b, column-major at W + j 2b b) is written for the second product.  A reflector
+// with tau = 0 (a task that never ran) is a zero column.  One block of 256 threads per D_j.
+template <class T>
+__global__ void __launch_bounds__(256) k_wy_level(int n, int b, int L, int ngroups, int g_lo, int w00, int ntask,
+                                                  const T* V2, const T* tau2, T* W) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int j = blockIdx.x, tid = threadIdx.x;
+  const int g = g_lo + j, t = L - (ngroups - 1 - g);
+  const int m = 2 * b;
+  T* Vs = reinterpret_cast<T*>(smraw);  // 2b x b
+  T* Ts = Vs + (size_t)m * b;           // b x b
+  T* z = Ts + (size_t)b * b;            // b
+  T* taus = z + b;                      // b
+  const int w0 = w00 + m * j;
+  for (int idx = tid; idx < m * b; idx += blockDim.x) {
+    const int r = idx % m, q = idx / m;
+    const int sw = g * b + q, rel = r - q;
+    T v = zero_<T>();
+    if (sw <= n - 3 && rel >= 0 && rel < b && w0 + r < n) {
+      const long long rid = (long long)sw * ntask + t;
+      if (tau2[rid] != zero_<T>()) v = V2[rid * b + rel];
+    }
+    Vs[idx] = v;
+  }
+  for (int q = tid; q < b; q += blockDim.x) {
+    const int sw = g * b + q;
+    taus[q] = (sw <= n - 3) ? tau2[(long long)sw * ntask + t] : zero_<T>();
+  }
+  for (int idx = tid; idx < b * b; idx += blockDim.x) Ts[idx] = zero_<T>();
+  __syncthreads();
+  for (int q = 0; q < b; ++q) {
+    // z_p = v_p^H v_q for p < q (overlap rows q .. p + b - 1)
+    for (int p = tid; p < q; p += blockDim.x) {
+      T acc = zero_<T>();
+      for (int r = q; r < p + b; ++r) acc += cmul(Vs[r + p * m], Vs[r + q * m]);
+      z[p] = acc;
+    }
+    __syncthreads();
+    const T tq = taus[q];
+    for (int p = tid; p < q; p += blockDim.x) {
+      T acc = zero_<T>();
+      for (int l = p; l < q; ++l) acc += Ts[p + l * b] * z[l];
+      Ts[p + q * b] = -(tq * acc);
+    }
+    if (tid == 0) Ts[q + q * b] = tq;
+    __syncthreads();
+  }
+  // W = V T: W(r, q) = sum_{p <= q} V(r, p) T(p, q), V(r, p) != 0 for r - b < p <= r
+  T* Wj = W + (size_t)j * m * b;
+  for (int idx = tid; idx < m * b; idx += blockDim.x) {
+    const int r = idx % m, q = idx / m;
+    const int p0 = max(0, r - b + 1), p1 = min(q, r);
+    T acc = zero_<T>();
+    for (int p = p0; p <= p1; ++p) acc += Vs[r + p * m] * Ts[p + q * b];
+    Wj[idx] = acc;
+  }
+}
+
 template <class T> size_t bulge_smem(int b) { return sizeof(T) * ((size_t)3 * b * (b + 1) + 3 * b + 4 * 64) + 64; }
 
 }  // namespace
@@ -484,6 +548,65 @@ template <class T> int hb2st(Sys& s, double* d, double* e) {
 
 template <class T, int COLS> int bt_levels(Sys& s, int n, int k, int b, T* Y, int ldy);
 
+// The blocks of level L: groups g in [g_lo, g_lo + nblk) with task t = L - (ngroups - 1 - g) in
+// range and a window start w0(g) = (g + t) b + 1 below n; w00 = w0(g_lo); windows are 2b apart.
+struct LevelBlocks {
+  int g_lo, nblk, w00;
+};
+inline LevelBlocks level_blocks(int n, int b, int L, int ngroups, int ntask) {
+  LevelBlocks lb{0, 0, 0};
+  const int g_lo = std::max(0, ngroups - 1 - L);
+  int g_hi = std::min(ngroups - 1, ntask - 1 + ngroups - 1 - L);
+  auto w0 = [&](int g) { return (2 * g + L - ngroups + 1) * b + 1; };
+  while (g_hi >= g_lo && w0(g_hi) >= n) --g_hi;
+  if (g_hi < g_lo) return lb;
+  lb.g_lo = g_lo;
+  lb.nblk = g_hi - g_lo + 1;
+  lb.w00 = w0(g_lo);
+  return lb;
+}
+
+// Y <- Q2 Y with every level applied as  P = blockdiag(V_j^H) Y_L,  Y_L -= blockdiag(V_j T_j) P  on the
+// emulated FP64 product engine (Y_L: the level's rows).  Returns GEV_ERR_UNSUPPORTED, before
+// launching anything, when the handle's scratch cannot hold a level's product.
+template <class T> int bt_levels_wy(Sys& s, int n, int k, int b, T* Y, int ldy) {
+  constexpr int cx = is_cx<T>::value ? 1 : 0;
+  const int ngroups = (n - 3) / b + 1;
+  const int nlevels = ngroups + s.ntask;
+  T* P = (T*)s.W1;  // (nblk b) x k products V^H Y (W1 is free during the back-transform)
+  T* Wb = (T*)s.Q;  // the level's W_j blocks, nblk x 2b x b
+  size_t need = 0;
+  int max_nblk = 0;
+  for (int L = 0; L < nlevels; ++L) {
+    const LevelBlocks lb = level_blocks(n, b, L, ngroups, s.ntask);
+    if (lb.nblk == 0) continue;
+    max_nblk = std::max(max_nblk, lb.nblk);
+    const int rows = std::min(lb.nblk * 2 * b, n - lb.w00);
+    need = std::max(need, gemm_f64_bdiag_scratch(lb.nblk * b, k, rows, b, 2 * b, cx));
+    need = std::max(need, gemm_f64_bdiag_scratch(rows, k, lb.nblk * b, 2 * b, b, cx));
+  }
+  if (need > s.ozws_bytes || (size_t)max_nblk * b * k * sizeof(T) > (size_t)n * n * sizeof(T) ||
+      (size_t)max_nblk * 2 * b * b * sizeof(T) > (size_t)n * n * sizeof(double))
+    return GEV_ERR_UNSUPPORTED;
+  const size_t smem = sizeof(T) * ((size_t)2 * b * b + (size_t)b * b + 2 * b) + 64;
+  GEV_TRY(allow_dyn_smem(k_wy_level<T>, smem));
+  for (int L = 0; L < nlevels; ++L) {
+    const LevelBlocks lb = level_blocks(n, b, L, ngroups, s.ntask);
+    if (lb.nblk == 0) continue;
+    const int rows = std::min(lb.nblk * 2 * b, n - lb.w00);
+    GEV_COUNT(s);
+    k_wy_level<T><<<lb.nblk, 256, smem, s.stream>>>(n, b, L, ngroups, lb.g_lo, lb.w00, s.ntask, (const T*)s.V2,
+                                                    (const T*)s.tau2, Wb);
+    BdOp a1{1, cx, b, n, s.ntask, lb.g_lo, L, ngroups, lb.nblk, lb.w00, s.V2, s.tau2, nullptr};
+    T* Yl = Y + lb.w00;
+    const int M1 = lb.nblk * b;
+    if (!gemm_f64_bdiag(s, M1, k, rows, a1, b, 2 * b, Yl, ldy, 1.0, 0.0, P, M1)) return GEV_ERR_CUDA;
+    BdOp a2{2, cx, b, n, s.ntask, lb.g_lo, L, ngroups, lb.nblk, lb.w00, nullptr, nullptr, Wb};
+    if (!gemm_f64_bdiag(s, rows, k, M1, a2, 2 * b, b, P, M1, -1.0, 1.0, Yl, ldy)) return GEV_ERR_CUDA;
+  }
+  return last_error();
+}
+
 template <int B> int bt_levels_f32(Sys& s, int n, int k, float* Y, int ldy) {
   const int ngroups = (n - 3) / B + 1;
   const size_t smem = sizeof(float) * ((size_t)2 * B * (BTF_COLS + 1) + (size_t)B * B + B) + 64;
@@ -515,6 +638,14 @@ template <class T> int bt_hb2st(Sys& s, const double* Z, int ldz, int k, T* Y, i
     if (b == 16) return bt_levels_f32<16>(s, n, k, Y, ldy);
     if (b == 32) return bt_levels_f32<32>(s, n, k, Y, ldy);
     if (b == 64) return bt_levels_f32<64>(s, n, k, Y, ldy);
+  }
+  // FP64 data with the emulated product engine: each level as two block-diagonal tensor-core
+  // products of its compact-WY blocks
+  if constexpr (std::is_same<T, double>::value || std::is_same<T, zd>::value) {
+    if (s.emu_fp64) {
+      const int r = bt_levels_wy<T>(s, n, k, b, Y, ldy);
+      if (r != GEV_ERR_UNSUPPORTED) return r;  // else: the scratch is too small, take the level kernel
+    }
   }
   // level-parallel application (see k_bt_bulge_level); one thread per column, as many columns
   // per block as the staged window (2b rows) allows in shared memory

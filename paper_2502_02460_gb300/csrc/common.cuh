@@ -186,6 +186,28 @@ void gemm_account(Sys& s, int* calls, double* ms, double* flops);
 void gemm_f64_emulated(Sys& s, const GemmP<double>& p);
 void gemm_c128_emulated(Sys& s, const GemmP<zd>& p);  // real alpha, beta
 size_t gemm_f64_emulated_scratch(int M, int N, int K);  // bytes of s.ozws for an M x N x K product
+
+// A block-diagonal operand of the back-transform-2 products: the reflector blocks
+// D_j = H(s0) H(s0 + 1) ... H(s0 + b - 1) = I - V_j T_j V_j^H of one level of the band -> tridiagonal
+// back-transform (block j: group g = g_lo + j, task t = L - (ngroups - 1 - g), sweeps s0 = g b ..;
+// it acts on rows [w00 + 2 b j, w00 + 2 b j + 2 b)).
+//   kind 1: op(A) = blockdiag(V_j^H), b x 2b blocks (row q: the reflector of sweep s0 + q, read from
+//           the bulge-chasing store V2 / tau2; a reflector with tau = 0 counts as zero)
+//   kind 2: op(A) = blockdiag(W_j), 2b x b blocks, W_j = V_j T_j stored column-major at W + j 2b b
+// Complex data (cx) enter through the real 2 x 2 embedding like every emulated complex product.
+struct BdOp {
+  int kind, cx, b, n, ntask, g_lo, L, ngroups, nblk, w00;
+  const void* V2;
+  const void* tau2;
+  const void* W;
+};
+// C (M x N) = alpha op(A) B + beta C, op(A) the block-diagonal operand (blocks bm x bk; M, K, bm, bk in
+// complex units for complex data), B (K x N, ld ldb) and C (ld ldc) as stored, on the emulated FP64
+// product engine; each output tile reads only its blocks' K range.  Returns false (nothing launched)
+// when s.ozws is too small: gemm_f64_bdiag_scratch gives the bytes.
+bool gemm_f64_bdiag(Sys& s, int M, int N, int K, const BdOp& a, int bm, int bk, const void* B, long long ldb,
+                    double alpha, double beta, void* C, long long ldc);
+size_t gemm_f64_bdiag_scratch(int M, int N, int K, int bm, int bk, int cx);
 template <class T> GemmP<T> gp(int M, int N, int K, int ta, int tb, T alpha, const T* A, long long lda,
                                const T* B, long long ldb, T beta, T* C, long long ldc) {
   GemmP<T> p{};

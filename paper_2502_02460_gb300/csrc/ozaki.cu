@@ -239,6 +239,95 @@ __global__ void k_split(int R, int K, Opnd o, int fast_r, const int* E, int TR, 
   }
 }
 
+// K slices of a row tile of a block-diagonal op(A): the first slice of the tile's K range and the
+// count (bm, bk multiples of 16 that divide / are multiples of the 128-row tile)
+__host__ __device__ __forceinline__ void bd_range(int bm, int bk, int mt, int* first, int* count) {
+  if (bm <= OM) {
+    const int per = OM / bm;
+    *first = mt * per * bk / KS;
+    *count = per * bk / KS;
+  } else {
+    *first = (mt / (bm / OM)) * bk / KS;
+    *count = bk / KS;
+  }
+}
+
+// Entry (i, kk) (embedded units for complex data) of a block-diagonal back-transform-2 operand.
+__device__ __forceinline__ double bd_at(const BdOp& o, long long i, long long kk) {
+  const long long ir = o.cx ? (i >> 1) : i, kr = o.cx ? (kk >> 1) : kk;
+  const int b = o.b;
+  double x = 0.0, y = 0.0;
+  if (o.kind == 1) {  // V_j^H: row q of block j, column r of the block's window
+    const long long j = ir / b, q = ir % b, r = kr - 2LL * b * j;
+    if (r < 0 || r >= 2 * b || j >= o.nblk) return 0.0;
+    const long long g = o.g_lo + j, t = o.L - (o.ngroups - 1 - g), sw = g * b + q, rel = r - q;
+    if (sw > o.n - 3 || rel < 0 || rel >= b || o.w00 + 2LL * b * j + r >= o.n) return 0.0;
+    const long long rid = sw * o.ntask + t;
+    if (o.cx) {
+      const double2 tau = static_cast<const double2*>(o.tau2)[rid];
+      if (tau.x == 0.0 && tau.y == 0.0) return 0.0;
+      const double2 v = static_cast<const double2*>(o.V2)[rid * b + rel];
+      x = v.x;
+      y = -v.y;  // conjugate: op(A) = V^H
+    } else {
+      if (static_cast<const double*>(o.tau2)[rid] == 0.0) return 0.0;
+      return static_cast<const double*>(o.V2)[rid * b + rel];
+    }
+  } else {  // W_j: row r of block j, column q
+    const long long j = ir / (2 * b), r = ir % (2 * b), q = kr - (long long)b * j;
+    if (q < 0 || q >= b || j >= o.nblk) return 0.0;
+    const long long off = j * 2LL * b * b + r + q * 2LL * b;
+    if (o.cx) {
+      const double2 w = static_cast<const double2*>(o.W)[off];
+      x = w.x;
+      y = w.y;
+    } else {
+      return static_cast<const double*>(o.W)[off];
+    }
+  }
+  const long long a = i & 1, c = kk & 1;  // the 2 x 2 block [[x, -y], [y, x]]
+  return (a == c) ? x : (a == 0 ? -y : y);
+}
+
+// Row exponents and digit planes of a block-diagonal op(A) in the compact layout: row tile mt holds
+// only the slices of its K range (bd_range).  One warp per row of the padded MT x 128 rows; lane l
+// takes 8 consecutive columns of the range and writes 16 bytes to each plane.
+__global__ void k_split_bd(int M, BdOp o, int bm, int bk, int MT, int* E, unsigned char* out) {
+  const long long i = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= (long long)MT * OM) return;  // uniform per warp
+  const int mt = (int)(i / OM);
+  int f = 0, c = 0;
+  bd_range(bm, bk, mt, &f, &c);
+  const bool act = lane * 8 < c * KS;
+  double v[8];
+  int e = EXP_ZERO;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const long long kk = (long long)f * KS + lane * 8 + q;
+    v[q] = (act && i < M) ? bd_at(o, i, kk) : 0.0;
+    e = max(e, exp_above(v[q]));
+  }
+  e = __reduce_max_sync(0xffffffffu, e);
+  if (lane == 0) E[i] = e;
+  if (!act) return;
+  const int Er = clamp_exp(e);
+  uint16_t dg[8][NSLICE];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) digits(v[q], Er, dg[q]);
+  const int tile_bytes = OM * KS * 2;
+  unsigned char* base = out + (((long long)mt * c + (lane >> 1)) * NSLICE) * tile_bytes + toff((int)(i % OM), (lane & 1) * 8);
+#pragma unroll
+  for (int p = 0; p < NSLICE; ++p) {
+    uint4 w;
+    w.x = (uint32_t)dg[0][p] | ((uint32_t)dg[1][p] << 16);
+    w.y = (uint32_t)dg[2][p] | ((uint32_t)dg[3][p] << 16);
+    w.z = (uint32_t)dg[4][p] | ((uint32_t)dg[5][p] << 16);
+    w.w = (uint32_t)dg[6][p] | ((uint32_t)dg[7][p] << 16);
+    *reinterpret_cast<uint4*>(base + (long long)p * tile_bytes) = w;
+  }
+}
+
 struct OzP {
   int M, N, K, koff, c_lower, tri_a, tri_b, cx;  // cx: complex product in the real embedding
   int MT, NT, KT, ksplit;
@@ -251,7 +340,11 @@ struct OzP {
   const int* E;
   const int* F;
   int* status;
+  // block-diagonal op(A) (0: off): block j has rows [j bd_bm, (j+1) bd_bm) and its non-zero columns
+  // [j bd_bk, (j+1) bd_bk); the A planes then hold, per row tile, only that tile's K range (compact)
+  int bd_bm, bd_bk;
 };
+
 
 // an exact FP32 chunk sum (a multiple of 2^-49 below 2^8 in magnitude) in units of 2^-49
 __device__ __forceinline__ long long units49(uint32_t b) {
@@ -303,6 +396,16 @@ __global__ void __launch_bounds__(NTH, 1) ozaki_kernel(OzP p) {
   ke <<= rs;
   int s_lo = (int)(kb / KS), s_hi = (int)(ke > 0 ? (ke + KS - 1) / KS : 0);
   if (s_hi < s_lo) s_hi = s_lo;
+  // A-plane slices: a_kt per row tile, slice kt read at kt - a_off
+  int a_kt = p.KT, a_off = 0;
+  if (p.bd_bm) {
+    int f = 0, c = 0;
+    bd_range(p.bd_bm, p.bd_bk, mt, &f, &c);
+    s_lo = min(f, p.KT);
+    s_hi = min(f + c, p.KT);
+    a_kt = c;
+    a_off = f;
+  }
   if (p.ksplit > 1) {  // this CTA's share of the slices
     const int tot = s_hi - s_lo, z = blockIdx.y;
     const int a = s_lo + (int)((long long)tot * z / p.ksplit);
@@ -348,7 +451,7 @@ __global__ void __launch_bounds__(NTH, 1) ozaki_kernel(OzP p) {
   if (warp == NEPI_W) {
     // ---- copy warp: digit-plane slices into the stage ring
     if (lane == 0) {
-      const unsigned char* a_src = p.Ap + (long long)mt * p.KT * A_STAGE;
+      const unsigned char* a_src = p.Ap + ((long long)mt * a_kt - a_off) * A_STAGE;
       const unsigned char* b_src = p.Bp + (long long)nt * p.KT * B_STAGE;
       for (int s = 0; s < nst; ++s) {
         const int slot = s % NSTAGE;
@@ -654,6 +757,79 @@ void gemm_c128_emulated(Sys& s, const GemmP<zd>& q) {
   Opnd b{q.B, q.tb ? 1 : q.ldb, q.tb ? q.ldb : 1, keep_b_of(q.tri_b), 2, q.tb == 2 ? 1 : 0, 0};
   emulate(s, 2 * q.M, q.N, 2 * q.K, a, sizeof(zd) * (size_t)a.sk, b, sizeof(zd) * (size_t)b.sk, q.tri_a, q.tri_b,
           q.c_lower, 1, q.alpha.x, q.beta.x, reinterpret_cast<double*>(q.C), 2 * q.ldc);
+}
+
+namespace {
+
+struct BdLayout {
+  size_t Mp, Np, f_off, a_off, b_off, total;
+  int MT, NT, KT, acount;
+};
+
+// scratch of a block-diagonal product (embedded units): row exponents, column exponents, the compact
+// A planes (acount slices per row tile) and the B planes over the whole K (no piece limit: a tile
+// sums at most 16 slices, far below the int64 accumulator's range)
+BdLayout bd_layout(int Me, int N, int Ke, int bme, int bke) {
+  BdLayout L;
+  L.Mp = rup(std::max(Me, 1), OM);
+  L.Np = rup(std::max(N, 1), ON);
+  L.MT = (int)(L.Mp / OM);
+  L.NT = (int)(L.Np / ON);
+  L.KT = (std::max(Ke, 1) + KS - 1) / KS;
+  int f = 0;
+  bd_range(bme, bke, 0, &f, &L.acount);
+  L.f_off = rup(L.Mp * sizeof(int), 256);
+  L.a_off = L.f_off + rup(L.Np * sizeof(int), 256);
+  L.b_off = L.a_off + (size_t)L.MT * L.acount * A_STAGE;
+  L.total = L.b_off + (size_t)L.NT * L.KT * B_STAGE;
+  return L;
+}
+
+}  // namespace
+
+size_t gemm_f64_bdiag_scratch(int M, int N, int K, int bm, int bk, int cx) {
+  const int e = cx ? 2 : 1;
+  return bd_layout(e * M, N, e * K, e * bm, e * bk).total;
+}
+
+bool gemm_f64_bdiag(Sys& s, int M, int N, int K, const BdOp& a, int bm, int bk, const void* B, long long ldb,
+                    double alpha, double beta, void* C, long long ldc) {
+  if (M <= 0 || N <= 0) return true;
+  const int rs = a.cx ? 1 : 0;
+  const int Me = M << rs, Ke = K << rs, bme = bm << rs, bke = bk << rs;
+  const BdLayout L = bd_layout(Me, N, Ke, bme, bke);
+  if (!s.ozws || L.total > s.ozws_bytes) return false;
+  if (allow_dyn_smem(ozaki_kernel, SMEM_OZ) != 0) return false;
+  unsigned char* base = static_cast<unsigned char*>(s.ozws);
+  int* E = reinterpret_cast<int*>(base);
+  int* F = reinterpret_cast<int*>(base + L.f_off);
+  unsigned char* Ap = base + L.a_off;
+  unsigned char* Bp = base + L.b_off;
+  // op(B) column j, element k: B[k + j ldb] (complex: the re / im parts of element k / 2)
+  const Opnd b{B, ldb, 1, 0, a.cx ? 2 : 0, 0, 0};
+  cudaMemsetAsync(F, 0x80, L.Np * sizeof(int), s.stream);
+  GEV_COUNT(s);
+  k_split_bd<<<cdiv((long long)L.MT * OM * 32, 256), 256, 0, s.stream>>>(Me, a, bme, bke, L.MT, E, Ap);
+  if (Ke > 0) {
+    GEV_COUNT(s);
+    k_vec_exp<<<dim3(cdiv(N, 8), cdiv(Ke, 1024)), dim3(32, 8), 0, s.stream>>>(N, Ke, b, 0, F);
+    GEV_COUNT(s);
+    k_split<<<cdiv((long long)L.NT * ON * 2 * L.KT, 256), 256, 0, s.stream>>>(N, Ke, b, 0, F, ON, L.NT, L.KT, Bp);
+  }
+  OzP p{};
+  p.M = Me; p.N = N; p.K = Ke; p.koff = 0; p.c_lower = 0;
+  p.tri_a = 0; p.tri_b = 0; p.cx = rs;
+  p.MT = L.MT; p.NT = L.NT; p.KT = L.KT; p.ksplit = 1;
+  p.alpha = alpha; p.beta = beta;
+  p.C = static_cast<double*>(C);
+  p.ldc = ldc << rs;
+  p.ws = nullptr;
+  p.Ap = Ap; p.Bp = Bp; p.E = E; p.F = F; p.status = s.status;
+  p.bd_bm = bme;
+  p.bd_bk = bke;
+  GEV_COUNT(s);
+  ozaki_kernel<<<dim3(L.MT * L.NT, 1), NTH, SMEM_OZ, s.stream>>>(p);
+  return true;
 }
 
 }  // namespace gev
