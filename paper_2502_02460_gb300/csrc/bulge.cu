@@ -571,6 +571,7 @@ inline LevelBlocks level_blocks(int n, int b, int L, int ngroups, int ntask) {
 // launching anything, when the handle's scratch cannot hold a level's product.
 template <class T> int bt_levels_wy(Sys& s, int n, int k, int b, T* Y, int ldy) {
   constexpr int cx = is_cx<T>::value ? 1 : 0;
+  constexpr bool f32 = std::is_same<T, float>::value;
   const int ngroups = (n - 3) / b + 1;
   const int nlevels = ngroups + s.ntask;
   T* P = (T*)s.W1;  // (nblk b) x k products V^H Y (W1 is free during the back-transform)
@@ -582,8 +583,13 @@ template <class T> int bt_levels_wy(Sys& s, int n, int k, int b, T* Y, int ldy) 
     if (lb.nblk == 0) continue;
     max_nblk = std::max(max_nblk, lb.nblk);
     const int rows = std::min(lb.nblk * 2 * b, n - lb.w00);
-    need = std::max(need, gemm_f64_bdiag_scratch(lb.nblk * b, k, rows, b, 2 * b, cx));
-    need = std::max(need, gemm_f64_bdiag_scratch(rows, k, lb.nblk * b, 2 * b, b, cx));
+    if constexpr (f32) {
+      need = std::max(need, gemm_f32_bdiag_scratch(lb.nblk * b, k, rows, b, 2 * b));
+      need = std::max(need, gemm_f32_bdiag_scratch(rows, k, lb.nblk * b, 2 * b, b));
+    } else {
+      need = std::max(need, gemm_f64_bdiag_scratch(lb.nblk * b, k, rows, b, 2 * b, cx));
+      need = std::max(need, gemm_f64_bdiag_scratch(rows, k, lb.nblk * b, 2 * b, b, cx));
+    }
   }
   if (need > s.ozws_bytes || (size_t)max_nblk * b * k * sizeof(T) > (size_t)n * n * sizeof(T) ||
       (size_t)max_nblk * 2 * b * b * sizeof(T) > (size_t)n * n * sizeof(double))
@@ -600,9 +606,14 @@ template <class T> int bt_levels_wy(Sys& s, int n, int k, int b, T* Y, int ldy) 
     BdOp a1{1, cx, b, n, s.ntask, lb.g_lo, L, ngroups, lb.nblk, lb.w00, s.V2, s.tau2, nullptr};
     T* Yl = Y + lb.w00;
     const int M1 = lb.nblk * b;
-    if (!gemm_f64_bdiag(s, M1, k, rows, a1, b, 2 * b, Yl, ldy, 1.0, 0.0, P, M1)) return GEV_ERR_CUDA;
     BdOp a2{2, cx, b, n, s.ntask, lb.g_lo, L, ngroups, lb.nblk, lb.w00, nullptr, nullptr, Wb};
-    if (!gemm_f64_bdiag(s, rows, k, M1, a2, 2 * b, b, P, M1, -1.0, 1.0, Yl, ldy)) return GEV_ERR_CUDA;
+    if constexpr (f32) {
+      if (!gemm_f32_bdiag(s, M1, k, rows, a1, b, 2 * b, Yl, ldy, 1.f, 0.f, P, M1)) return GEV_ERR_CUDA;
+      if (!gemm_f32_bdiag(s, rows, k, M1, a2, 2 * b, b, P, M1, -1.f, 1.f, Yl, ldy)) return GEV_ERR_CUDA;
+    } else {
+      if (!gemm_f64_bdiag(s, M1, k, rows, a1, b, 2 * b, Yl, ldy, 1.0, 0.0, P, M1)) return GEV_ERR_CUDA;
+      if (!gemm_f64_bdiag(s, rows, k, M1, a2, 2 * b, b, P, M1, -1.0, 1.0, Yl, ldy)) return GEV_ERR_CUDA;
+    }
   }
   return last_error();
 }
@@ -635,6 +646,11 @@ template <class T> int bt_hb2st(Sys& s, const double* Z, int ldz, int k, T* Y, i
   }
   if (n <= 2) return 0;
   if constexpr (std::is_same<T, float>::value) {
+    // mixed form with the FP32 tensor products: each level as two block-diagonal BF16x6 products
+    if (s.fp32_tc) {
+      const int r = bt_levels_wy<float>(s, n, k, b, Y, ldy);
+      if (r != GEV_ERR_UNSUPPORTED) return r;  // else: the scratch is too small, take the level kernel
+    }
     if (b == 16) return bt_levels_f32<16>(s, n, k, Y, ldy);
     if (b == 32) return bt_levels_f32<32>(s, n, k, Y, ldy);
     if (b == 64) return bt_levels_f32<64>(s, n, k, Y, ldy);

@@ -208,6 +208,11 @@ struct BdOp {
 bool gemm_f64_bdiag(Sys& s, int M, int N, int K, const BdOp& a, int bm, int bk, const void* B, long long ldb,
                     double alpha, double beta, void* C, long long ldc);
 size_t gemm_f64_bdiag_scratch(int M, int N, int K, int bm, int bk, int cx);
+// The same in FP32 from BF16x6 (or x3, s.fp32_tc) split products on the tensor cores (tc_gemm.cu);
+// real data only.
+bool gemm_f32_bdiag(Sys& s, int M, int N, int K, const BdOp& a, int bm, int bk, const float* B, long long ldb,
+                    float alpha, float beta, float* C, long long ldc);
+size_t gemm_f32_bdiag_scratch(int M, int N, int K, int bm, int bk);
 template <class T> GemmP<T> gp(int M, int N, int K, int ta, int tb, T alpha, const T* A, long long lda,
                                const T* B, long long ldb, T beta, T* C, long long ldc) {
   GemmP<T> p{};

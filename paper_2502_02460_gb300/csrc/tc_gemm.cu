@@ -92,7 +92,79 @@ struct TcP {
   const unsigned char* Ap;
   const unsigned char* Bp;
   int* status;
+  int nstage;  // stages of the shared-memory ring (<= NSTAGE; the launch's dynamic shared memory)
+  // block-diagonal op(A) (0: off): block j has rows [j bd_bm, (j+1) bd_bm) and its non-zero columns
+  // [j bd_bk, (j+1) bd_bk); the A planes then hold, per row tile, only that tile's K range (compact)
+  int bd_bm, bd_bk;
 };
+
+// K slices of a row tile of a block-diagonal op(A): the first slice of the tile's K range and the
+// count (bm, bk multiples of 16 that divide / are multiples of the 128-row tile)
+__host__ __device__ __forceinline__ void bd_range32(int bm, int bk, int mt, int* first, int* count) {
+  if (bm <= TM) {
+    const int per = TM / bm;
+    *first = mt * per * bk / KS;
+    *count = per * bk / KS;
+  } else {
+    *first = (mt / (bm / TM)) * bk / KS;
+    *count = bk / KS;
+  }
+}
+
+// Entry (i, kk) of a real block-diagonal back-transform-2 operand in FP32 (BdOp, common.cuh).
+__device__ __forceinline__ float bd_at32(const BdOp& o, long long i, long long kk) {
+  const int b = o.b;
+  if (o.kind == 1) {  // V_j^H: row q of block j, column r of the block's window
+    const long long j = i / b, q = i % b, r = kk - 2LL * b * j;
+    if (r < 0 || r >= 2 * b || j >= o.nblk) return 0.f;
+    const long long g = o.g_lo + j, t = o.L - (o.ngroups - 1 - g), sw = g * b + q, rel = r - q;
+    if (sw > o.n - 3 || rel < 0 || rel >= b || o.w00 + 2LL * b * j + r >= o.n) return 0.f;
+    const long long rid = sw * o.ntask + t;
+    if (static_cast<const float*>(o.tau2)[rid] == 0.f) return 0.f;
+    return static_cast<const float*>(o.V2)[rid * b + rel];
+  }
+  const long long j = i / (2 * b), r = i % (2 * b), q = kk - (long long)b * j;  // W_j: row r, column q
+  if (q < 0 || q >= b || j >= o.nblk) return 0.f;
+  return static_cast<const float*>(o.W)[j * 2LL * b * b + r + q * 2LL * b];
+}
+
+// The three BF16 planes of a block-diagonal op(A) in the compact layout (row tile mt holds only the
+// slices of its K range).  One warp per row of the padded MT x 128 rows; lane l takes 8 consecutive
+// columns of the range and writes 16 bytes to each plane.
+__global__ void k_split3_bd(int M, BdOp o, int bm, int bk, int MT, unsigned char* out) {
+  const long long i = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= (long long)MT * TM) return;
+  const int mt = (int)(i / TM);
+  int f = 0, c = 0;
+  bd_range32(bm, bk, mt, &f, &c);
+  if (lane * 8 >= c * KS) return;
+  uint32_t pk[NPL][4];
+#pragma unroll
+  for (int q = 0; q < 8; q += 2) {
+    uint16_t h[2][NPL];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const long long kk = (long long)f * KS + lane * 8 + q + u;
+      const float x = (i < M) ? bd_at32(o, i, kk) : 0.f;
+      const __nv_bfloat16 x1 = __float2bfloat16_rn(x);
+      const float r1 = x - __bfloat162float(x1);  // exact
+      const __nv_bfloat16 x2 = __float2bfloat16_rn(r1);
+      const float r2 = r1 - __bfloat162float(x2);  // exact
+      const __nv_bfloat16 x3 = __float2bfloat16_rn(r2);
+      h[u][0] = __bfloat16_as_ushort(x1);
+      h[u][1] = __bfloat16_as_ushort(x2);
+      h[u][2] = __bfloat16_as_ushort(x3);
+    }
+#pragma unroll
+    for (int p = 0; p < NPL; ++p) pk[p][q / 2] = (uint32_t)h[0][p] | ((uint32_t)h[1][p] << 16);
+  }
+  const int plane_bytes = TM * KS * 2;
+  unsigned char* base = out + (((long long)mt * c + (lane >> 1)) * NPL) * plane_bytes + toff16((int)(i % TM), (lane & 1) * 8);
+#pragma unroll
+  for (int p = 0; p < NPL; ++p)
+    *reinterpret_cast<uint4*>(base + (long long)p * plane_bytes) = make_uint4(pk[p][0], pk[p][1], pk[p][2], pk[p][3]);
+}
 
 __global__ void __launch_bounds__(NTH, 1) tc32_kernel(TcP p) {
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -108,6 +180,17 @@ __global__ void __launch_bounds__(NTH, 1) tc32_kernel(TcP p) {
   tile_k_range(p.tri_a, p.tri_b, m0, TM, n0, TN, p.K, 0, kb, ke);
   int s_lo = (int)(kb > 0 ? kb / KS : 0), s_hi = (int)(ke > 0 ? (ke + KS - 1) / KS : 0);
   if (s_hi < s_lo) s_hi = s_lo;
+  // A-plane slices: a_kt per row tile, slice kt read at kt - a_off
+  int a_kt = p.KT, a_off = 0;
+  if (p.bd_bm) {
+    int f = 0, c = 0;
+    bd_range32(p.bd_bm, p.bd_bk, mt, &f, &c);
+    s_lo = min(f, p.KT);
+    s_hi = min(f + c, p.KT);
+    a_kt = c;
+    a_off = f;
+  }
+  const int nstage = p.nstage;
   if (p.ksplit > 1) {
     const int tot = s_hi - s_lo, z = blockIdx.y;
     const int a = s_lo + (int)((long long)tot * z / p.ksplit);
@@ -117,7 +200,7 @@ __global__ void __launch_bounds__(NTH, 1) tc32_kernel(TcP p) {
   }
   const int nst = s_hi - s_lo;
 
-  unsigned char* ctrl = smem + NSTAGE * STAGE;
+  unsigned char* ctrl = smem + nstage * STAGE;
   uint64_t* full = reinterpret_cast<uint64_t*>(ctrl);
   uint64_t* empty = full + NSTAGE;
   uint64_t* accd = empty + NSTAGE;  // accumulator complete
@@ -126,7 +209,7 @@ __global__ void __launch_bounds__(NTH, 1) tc32_kernel(TcP p) {
   int* issued = reinterpret_cast<int*>(ctrl + 384);
   int* consumed = reinterpret_cast<int*>(ctrl + 448);
   if (tid == 0) {
-    for (int s = 0; s < NSTAGE; ++s) {
+    for (int s = 0; s < nstage; ++s) {
       mbar_init(su32(&full[s]), 1);
       mbar_init(su32(&empty[s]), 1);
     }
@@ -145,11 +228,11 @@ __global__ void __launch_bounds__(NTH, 1) tc32_kernel(TcP p) {
   if (warp == NEPI_W) {
     // ---- copy warp
     if (lane == 0) {
-      const unsigned char* a_src = p.Ap + (long long)mt * p.KT * A_ST;
+      const unsigned char* a_src = p.Ap + ((long long)mt * a_kt - a_off) * A_ST;
       const unsigned char* b_src = p.Bp + (long long)nt * p.KT * B_ST;
       for (int s = 0; s < nst; ++s) {
-        const int slot = s % NSTAGE;
-        if (s >= NSTAGE && !bar_wait(su32(&empty[slot]), ((s / NSTAGE) - 1) & 1, err)) {
+        const int slot = s % nstage;
+        if (s >= nstage && !bar_wait(su32(&empty[slot]), ((s / nstage) - 1) & 1, err)) {
           if (!*err) *err = 421;
           break;
         }
@@ -167,8 +250,8 @@ __global__ void __launch_bounds__(NTH, 1) tc32_kernel(TcP p) {
     if (lane == 0) {
       const uint32_t id = idesc_bf16(TM, TN);
       for (int s = 0; s < nst; ++s) {
-        const int slot = s % NSTAGE;
-        if (!bar_wait(su32(&full[slot]), (s / NSTAGE) & 1, err)) {
+        const int slot = s % nstage;
+        if (!bar_wait(su32(&full[slot]), (s / nstage) & 1, err)) {
           if (!*err) *err = 422;
           break;
         }
@@ -246,7 +329,7 @@ __global__ void __launch_bounds__(NTH, 1) tc32_kernel(TcP p) {
   __syncthreads();
   if (tid == 0 && *err) {
     // a wait gave up: let the copies already issued land before the shared memory is released
-    for (int s = *consumed; s < *issued; ++s) bar_wait_plain(su32(&full[s % NSTAGE]), (s / NSTAGE) & 1);
+    for (int s = *consumed; s < *issued; ++s) bar_wait_plain(su32(&full[s % nstage]), (s / nstage) & 1);
     atomicCAS(&p.status[ST_TIMEOUT], 0, *err);
   }
   fence_before();
@@ -310,6 +393,7 @@ bool gemm_tc32(Sys& s, const GemmP<TI>& q, TO* C, float alpha, float beta, int n
   p.M = q.M; p.N = q.N; p.K = std::max(q.K, 0); p.c_lower = q.c_lower; p.tri_a = q.tri_a; p.tri_b = q.tri_b;
   p.MT = MT; p.NT = NT; p.KT = KT; p.nprod = nprod; p.c_f64 = std::is_same<TO, double>::value ? 1 : 0;
   p.alpha = alpha; p.beta = beta; p.C = C; p.ldc = q.ldc; p.Ap = Ap; p.Bp = Bp; p.status = s.status;
+  p.nstage = NSTAGE;
   long long tiles = (long long)MT * NT;
   if (q.c_lower) tiles = (tiles + MT) / 2;
   int ks = 1;
@@ -328,6 +412,63 @@ bool gemm_tc32(Sys& s, const GemmP<TI>& q, TO* C, float alpha, float beta, int n
     GEV_COUNT(s);
     k_tc_reduce<TO><<<blocks, 256, 0, s.stream>>>(q.M, q.N, ks, q.c_lower, alpha, p.ws, beta, C, q.ldc);
   }
+  return true;
+}
+
+namespace {
+
+struct BdLayout32 {
+  size_t a_off, b_off, total;
+  int MT, NT, KT, acount;
+};
+
+BdLayout32 bd_layout32(int M, int N, int K, int bm, int bk) {
+  BdLayout32 L;
+  L.MT = (int)(rup(std::max(M, 1), TM) / TM);
+  L.NT = (int)(rup(std::max(N, 1), TN) / TN);
+  L.KT = (std::max(K, 1) + KS - 1) / KS;
+  int f = 0;
+  bd_range32(bm, bk, 0, &f, &L.acount);
+  L.a_off = 0;
+  L.b_off = rup((size_t)L.MT * L.acount * A_ST, 256);
+  L.total = L.b_off + (size_t)L.NT * L.KT * B_ST;
+  return L;
+}
+
+}  // namespace
+
+size_t gemm_f32_bdiag_scratch(int M, int N, int K, int bm, int bk) { return bd_layout32(M, N, K, bm, bk).total; }
+
+// C (M x N) = alpha op(A) B + beta C in FP32, op(A) a real block-diagonal operand (BdOp with FP32
+// data, blocks bm x bk), from BF16x6 split products; each output tile reads only its K range (4 or
+// 16 slices).  A three-stage ring keeps two CTAs on an SM (shared memory 109 KB, tensor memory 256
+// columns each), so one CTA's epilogue overlaps the other's products.
+bool gemm_f32_bdiag(Sys& s, int M, int N, int K, const BdOp& a, int bm, int bk, const float* B, long long ldb,
+                    float alpha, float beta, float* C, long long ldc) {
+  if (M <= 0 || N <= 0) return true;
+  const BdLayout32 L = bd_layout32(M, N, K, bm, bk);
+  if (!s.ozws || L.total > s.ozws_bytes) return false;
+  if (allow_dyn_smem(tc32_kernel, SMEM_TC) != 0) return false;
+  unsigned char* Ap = static_cast<unsigned char*>(s.ozws) + L.a_off;
+  unsigned char* Bp = static_cast<unsigned char*>(s.ozws) + L.b_off;
+  GEV_COUNT(s);
+  k_split3_bd<<<cdiv((long long)L.MT * TM * 32, 256), 256, 0, s.stream>>>(M, a, bm, bk, L.MT, Ap);
+  if (K > 0) {
+    GEV_COUNT(s);
+    k_split3<float><<<cdiv((long long)L.NT * TN * 2 * L.KT, 256), 256, 0, s.stream>>>(N, K, B, ldb, 1, 0, TN, L.NT,
+                                                                                   L.KT, Bp);
+  }
+  TcP p{};
+  p.M = M; p.N = N; p.K = std::max(K, 0); p.c_lower = 0; p.tri_a = 0; p.tri_b = 0;
+  p.MT = L.MT; p.NT = L.NT; p.KT = L.KT; p.nprod = s.fp32_tc == 3 ? 3 : 6; p.c_f64 = 0;
+  p.alpha = alpha; p.beta = beta; p.C = C; p.ldc = ldc; p.Ap = Ap; p.Bp = Bp; p.status = s.status;
+  p.ksplit = 1;
+  p.ws = nullptr;
+  p.bd_bm = bm;
+  p.bd_bk = bk;
+  p.nstage = std::min(3, L.acount);  // 109 KB of shared memory: two CTAs per SM
+  GEV_COUNT(s);
+  tc32_kernel<<<dim3(L.MT * L.NT, 1), NTH, (size_t)p.nstage * STAGE + 1024, s.stream>>>(p);
   return true;
 }
 
