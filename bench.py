@@ -211,6 +211,45 @@ def cpu_baseline(n_full: int, k_full: int, complex_: bool, seconds_target: float
                       f"({t:.2f} s), scaled by (N/{ns})^3 to N={n_full}"}
 
 
+def oracle_full_configs(threads_list=(None, 1), include_n4096=True):
+    """The FP64 CPU oracle, as it stands, timed IN FULL (no sampling, no scaling) on the two
+    configurations small enough for it: real N=512 with all 512 eigenpairs (seed 0) and real N=4096
+    with the k=1229 lowest (seed 1, 1e-8 cluster of 16).  N=512 runs at every thread count in
+    ``threads_list`` (None = all host cores); N=4096 at all host cores only (about a minute; a
+    single core would take about 20)."""
+    import numpy as np
+
+    import oracle
+    from paper_2502_02460_gb300 import inputs
+
+    oracle.lib()
+    cores = os.cpu_count() or 1
+    try:
+        import ctypes
+        omp = ctypes.CDLL("libgomp.so.1")
+        set_threads = omp.omp_set_num_threads
+        set_threads.argtypes = [ctypes.c_int]
+    except OSError:
+        set_threads = None
+    out = []
+    cases = [(512, 512, 0, False)] + ([(4096, 1229, 1, True)] if include_n4096 else [])
+    for n, k, seed, cluster in cases:
+        p = inputs.make_problem(n, k, seed=seed, cluster=cluster)
+        for th in (threads_list if n <= 512 else (None,)):
+            nt = cores if th is None else th
+            if set_threads is not None:
+                set_threads(nt)
+            t0 = time.perf_counter()
+            w, C, info, dg = oracle.gev(p.H, p.S, k)
+            t = time.perf_counter() - t0
+            out.append({"n": n, "k": k, "seed": seed, "threads": nt if set_threads else None, "s": t,
+                        "info": info, "max_abs_eig_err_vs_construction": float(np.max(np.abs(w - p.lam[:k]))),
+                        "resid": dg["resid"], "ortho": dg["ortho"]})
+    if set_threads is not None:
+        set_threads(cores)
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -248,10 +287,26 @@ def run_stream(args, dev, mixed=False):
     plan = serve.stream_plan(spec)
     cache = {}
     for (_, sid, it, n, k, last) in plan:  # build every request's pencil before the clock starts
+        on_gpu = n > 2048  # the construction's dense algebra through torch on the device (input only)
         if sid not in cache:
-            p = inputs.make_problem(n, k, seed=4000 + sid, complex_=True, gap_check=False)
-            cache[sid] = (p, gev.cm_from_numpy(p.S, dev))
+            p = inputs.make_problem(n, k, seed=4000 + sid, complex_=True, gap_check=False,
+                                    device=dev if on_gpu else None)
+            cache[sid] = (p, p.S if on_gpu else gev.cm_from_numpy(p.S, dev))
         p = cache[sid][0]
+        if on_gpu:  # p.H: column-major device buffer (the row-major buffer of H^T)
+            H0 = p.H
+            if it == 0:
+                cache[(sid, it)] = H0
+                continue
+            rng = np.random.default_rng(5000 + 1000 * sid + it)
+            G = torch.from_numpy(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))).to(dev)
+            dH = 0.5 * (G + G.conj().transpose(0, 1))
+            del G
+            dH = dH.transpose(0, 1).contiguous()  # column-major buffer of the Hermitian dH
+            scale = spec.dh_rel * torch.linalg.norm(H0) / torch.linalg.norm(dH)
+            cache[(sid, it)] = H0 + scale * dH
+            del dH
+            continue
         rng = np.random.default_rng(5000 + 1000 * sid + it)
         G = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
         dH = 0.5 * (G + G.conj().T)
@@ -277,6 +332,26 @@ def run_stream(args, dev, mixed=False):
                            f"N log-uniform in [{spec.n_min}, {spec.n_max}], 10 SCF iterations per "
                            f"system, S fixed, k = N/4)"})
     return st
+
+
+def run_stream_only(args):
+    """The k-point serving stream alone (plain FP64 and mixed), one JSON line."""
+    import torch
+
+    from paper_2502_02460_gb300 import build
+
+    build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    t0 = time.perf_counter()
+    plain = run_stream(args, dev)
+    mixed = run_stream(args, dev, mixed=True)
+    clk = clocks.stop()
+    print(json.dumps({"metric": "k-point stream p50/p99 ms, solves/s", "stream": plain, "stream_mixed": mixed,
+                      "wall_s": time.perf_counter() - t0, "clocks": clk}), flush=True)
+    return 0
 
 
 def time_density(solver, Cb, w, Sb, dev, stream, reps=5, warmup=3):
@@ -330,9 +405,19 @@ def main():
     ap.add_argument("--plain", dest="mixed", action="store_false", help="headline = plain FP64 form")
     ap.add_argument("--no-plain-beside", action="store_true",
                     help="do not time the plain FP64 solve beside the mixed headline")
+    ap.add_argument("--plain-steps", type=int, default=5,
+                    help="timed solves of the plain FP64 form (emulated products) beside the headline")
+    ap.add_argument("--plain-native-steps", type=int, default=3,
+                    help="timed solves of the plain FP64 form with native DMMA products")
+    ap.add_argument("--no-oracle-configs", action="store_true",
+                    help="skip timing the oracle in full on the N=512 and N=4096 configurations")
     ap.add_argument("--stream-requests", type=int, default=32,
                     help="requests of the k-point serving stream reported beside (0 = none)")
     ap.add_argument("--stream-n-max", type=int, default=2048)
+    ap.add_argument("--stream-full", action="store_true",
+                    help="the whole k-point stream: 512 requests, N log-uniform in [256, 8192]")
+    ap.add_argument("--stream-only", action="store_true",
+                    help="run only the k-point stream (both precisions) and print its line")
     ap.add_argument("--band-b", type=int, default=64)
     ap.add_argument("--fp32-products", type=int, default=-1, choices=[-1, 0, 3, 6],
                     help="mixed form, FP32 products: 6 / 3 = BF16x6 / BF16x3 on the tensor cores, "
@@ -343,13 +428,19 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-check", action="store_true",
+                    help="skip the on-device accuracy measurement of one extra solve")
     ap.add_argument("--no-density", action="store_true",
                     help="skip timing the density-matrix output of the benchmarked orbitals")
     ap.add_argument("--gen", default="auto", choices=["auto", "cpu", "gpu"],
                     help="where the synthetic pencil is built (auto: GPU for N > 4096)")
     args = ap.parse_args()
+    if args.stream_full:
+        args.stream_requests, args.stream_n_max = 512, 8192
     if args.impl == "reference":
         return run_reference(args)
+    if args.stream_only:
+        return run_stream_only(args)
 
     import torch
 
@@ -437,29 +528,35 @@ def main():
     if args.mixed and not args.no_plain_beside:
         solver.close()
 
-        def time_plain(emu):
+        def time_plain(emu, steps):
             ps = gev.Solver(args.n, complex_=args.complex, device=dev, mixed=False, band_b=args.band_b,
                             timing=1, stream=stream, fp64_emulation=emu)
             ps.solve_cm(Hb, Sb, args.k, w, Cb)
             torch.cuda.synchronize()
-            f0 = torch.cuda.Event(enable_timing=True)
-            f1 = torch.cuda.Event(enable_timing=True)
-            f0.record(stream)
-            ps.solve_cm(Hb, Sb, args.k, w, Cb)
-            f1.record(stream)
-            torch.cuda.synchronize()
-            out = {"value": f0.elapsed_time(f1) / 1e3, "unit": "s", "steps": 1, "warmup": 1,
+            times, steps_ms = [], []
+            for _ in range(steps):
+                f0 = torch.cuda.Event(enable_timing=True)
+                f1 = torch.cuda.Event(enable_timing=True)
+                f0.record(stream)
+                ps.solve_cm(Hb, Sb, args.k, w, Cb)
+                f1.record(stream)
+                torch.cuda.synchronize()
+                times.append(f0.elapsed_time(f1) / 1e3)
+                steps_ms.append(ps.last_report["ms"])
+            med_steps = {kk: statistics.median(r[kk] for r in steps_ms) for kk in gev.STEP_NAMES}
+            out = {"value": statistics.median(times), "unit": "s", "steps": steps, "warmup": 1,
+                   "per_step_s": times,
                    "fp64_products": "emulated (BF16 digit planes, tcgen05)" if emu else "native (DMMA)",
-                   "steps_ms": ps.last_report["ms"],
-                   "steps_roofline": steps_roofline(ps.last_report["ms"], args.n, args.k, args.band_b, args.complex,
+                   "steps_ms": med_steps,
+                   "steps_roofline": steps_roofline(med_steps, args.n, args.k, args.band_b, args.complex,
                                                     False, emu != 0, 0, args.fp32_products, mp),
                    "max_abs_eig_err_vs_construction": float(np.max(np.abs(w.cpu().numpy() - p.lam[: args.k])))}
             ps.close()
             return out
 
-        plain = time_plain(0)
+        plain = time_plain(0, args.plain_native_steps)
         if not args.complex:
-            plain_emu = time_plain(1)
+            plain_emu = time_plain(1, args.plain_steps)
         solver = gev.Solver(args.n, complex_=args.complex, device=dev, mixed=args.mixed,
                             band_b=args.band_b, timing=0, stream=stream, fp64_emulation=args.fp64_emulation,
                             fp32_products=args.fp32_products)
@@ -484,11 +581,26 @@ def main():
                "d2h_bytes_per_step": args.k * 8 + args.n * args.k * es}
         del Hd, Sd
     dens = None if args.no_density else time_density(solver, Cb, w, Sb, dev, stream)
+    # accuracy of the benchmarked configuration, measured on the device (gev_opts.check): the residual
+    # ||HC - SC Lambda||_1/(||H||_1 ||C||_1) and ||C^H S C - I||_1 of one more solve (not timed)
+    accuracy = None
+    if not args.no_check:
+        solver.close()
+        cs = gev.Solver(args.n, complex_=args.complex, device=dev, mixed=args.mixed, band_b=args.band_b,
+                        stream=stream, fp64_emulation=args.fp64_emulation, fp32_products=args.fp32_products,
+                        check=True)
+        cs.solve_cm(Hb, Sb, args.k, w, Cb)
+        accuracy = {"resid": cs.last_report["resid"], "ortho": cs.last_report["ortho"],
+                    "bound_resid": 1e-11 if args.mixed else 1e-13 * args.n ** 0.5,
+                    "bound_ortho": 1e-12 * args.n ** 0.5, "measured": "on the device (gev_opts.check)"}
+        cs.close()
     if rank != 0:
         if ws > 1:
             torch.distributed.barrier()
         return 0
     cb = None if args.no_cpu_baseline else cpu_baseline(args.n, args.k, args.complex)
+    if cb is not None and not args.no_oracle_configs:
+        cb["full_size_runs"] = oracle_full_configs()
     stream_stats = stream_mixed = None
     if args.stream_requests > 0 and ws == 1:
         del solver, Hb, Sb
@@ -512,6 +624,7 @@ def main():
         "stream": stream_stats,
         "stream_mixed": stream_mixed,
         "density": dens,
+        "accuracy": accuracy,
         "roofline": {"bound": "tensor", "kernel": roof_kernel,
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": None,

@@ -60,6 +60,9 @@ def lib() -> ctypes.CDLL:
             getattr(_lib, f"oracle_{p}_gev").restype = i
             getattr(_lib, f"oracle_{p}_density").argtypes = [i, i, dp, i, dp, dp, i]
             getattr(_lib, f"oracle_{p}_density").restype = None
+            getattr(_lib, f"oracle_{p}_gev_reduced").argtypes = [i, dp, i, dp, i, ctypes.c_double, i, dp, dp, i,
+                                                                   dp]
+            getattr(_lib, f"oracle_{p}_gev_reduced").restype = i
         _lib.oracle_d_steql.argtypes = [i, dp, dp, dp, dp, i]
         _lib.oracle_d_steql.restype = i
     return _lib
@@ -184,3 +187,21 @@ def gev(H: np.ndarray, S: np.ndarray, k: int):
                                                        max(n, 1), _ptr(dg))
     return w[:k].copy(), C[:, :k].copy(order="F"), int(info), {
         "resid": float(dg[0]), "ortho": float(dg[1]), "asym": float(dg[2])}
+
+
+def gev_reduced(H: np.ndarray, S: np.ndarray, delta: float, k: int):
+    """The k lowest eigenpairs of (H, S) in the basis of the eigenvectors of S with eigenvalue
+    >= delta (the procedure for an ill-conditioned S, section "Current Status of the
+    Implementation").  Returns ``(w, C, m, status)``: eigenvalues ascending, C = X Y (n x k, phase
+    normalised), the kept basis size m, status (0 ok, -1 no QL convergence, -2 bad arguments,
+    -3 k > m)."""
+    cx = np.iscomplexobj(H) or np.iscomplexobj(S)
+    H = _fortran(H, cx)
+    S = _fortran(S, cx)
+    n = H.shape[0]
+    w = np.zeros(max(k, 1))
+    C = np.zeros((n, max(k, 1)), dtype=H.dtype, order="F")
+    m = np.zeros(1, dtype=np.int32)
+    st = getattr(lib(), f"oracle_{_prefix(H)}_gev_reduced")(n, _ptr(H), n, _ptr(S), n, float(delta), k, _ptr(w),
+                                                            _ptr(C), max(n, 1), _ptr(m))
+    return w[:k].copy(), C[:, :k].copy(order="F"), int(m[0]), int(st)

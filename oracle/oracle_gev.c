@@ -431,6 +431,110 @@ out:
 }
 
 /* ---------------------------------------------------------------------------------------------
+ * Ill-conditioned overlap (section "Current Status of the Implementation", the paragraph on
+ * numerically singular S): the pencil is transformed to the basis of the eigenvectors D_i of S,
+ * omitting every D_i whose eigenvalue sigma_i is below delta, and the reduced standard problem is
+ * solved.  In the paper's order:
+ *   1. S = D diag(sigma) D^H  (one-stage tridiagonalisation + QL of the full Hermitian S, ascending),
+ *   2. keep the m eigenvectors with sigma_i >= delta: X = D_kept diag(sigma_kept)^{-1/2}  (n x m),
+ *   3. H~ = X^H H X  (m x m, plain products, Hermitian part kept),
+ *   4. H~ Y = Y Lambda  (one-stage tridiagonalisation + QL), the k lowest,
+ *   5. C = X Y, then the per-column phase normalisation.
+ * C^H S C = I on the kept space.  *m receives the kept count.  Returns 0; -1 when QL did not
+ * converge; -2 for bad arguments; -3 when k > m (fewer kept basis vectors than wanted pairs).
+ * ------------------------------------------------------------------------------------------- */
+static int herm_eig(int n, scalar* A, double* w, scalar* V) {
+  /* all eigenpairs of the full Hermitian A (overwritten): w ascending, V (n x n) */
+  double* d = (double*)malloc(sizeof(double) * n);
+  double* e = (double*)calloc((size_t)n, sizeof(double));
+  scalar* tau = (scalar*)malloc(sizeof(scalar) * n);
+  double* Zr = (double*)calloc((size_t)n * n, sizeof(double));
+  int* idx = (int*)malloc(sizeof(int) * n);
+  int st = 0;
+  FN(sytrd)(n, A, n, d, e, tau);
+  for (int i = 0; i < n; ++i) AT(Zr, n, i, i) = 1.0;
+  if (steql_impl(n, d, e, Zr, n)) { st = -1; goto out; }
+  stable_argsort(n, d, idx);
+  for (int c = 0; c < n; ++c) {
+    w[c] = d[idx[c]];
+    for (int i = 0; i < n; ++i) AT(V, n, i, c) = AT(Zr, n, i, idx[c]);
+  }
+  FN(ormtr)(n, n, A, n, tau, V, n);
+out:
+  free(d); free(e); free(tau); free(Zr); free(idx);
+  return st;
+}
+
+int FN(gev_reduced)(int n, const scalar* H, int ldh, const scalar* S, int lds, double delta, int k,
+                    double* w, scalar* C, int ldc, int* m_out) {
+  if (n < 1 || k < 1 || k > n || ldh < n || lds < n || ldc < n || !(delta >= 0.0)) return -2;
+  const size_t nn = (size_t)n * n;
+  scalar* A = (scalar*)malloc(sizeof(scalar) * nn);
+  scalar* D = (scalar*)malloc(sizeof(scalar) * nn);
+  double* sig = (double*)malloc(sizeof(double) * n);
+  int status = 0, m = 0;
+  scalar *X = NULL, *HX = NULL, *Ht = NULL, *Yt = NULL;
+  double* wt = NULL;
+  /* 1. eigenvectors of S */
+  for (int j = 0; j < n; ++j)
+    for (int i = 0; i < n; ++i) AT(A, n, i, j) = (i >= j) ? AT(S, lds, i, j) : CONJ(AT(S, lds, j, i));
+  if (herm_eig(n, A, sig, D)) { status = -1; goto out; }
+  /* 2. the kept basis: sigma ascending, so the kept ones are the last m */
+  int first = 0;
+  while (first < n && sig[first] < delta) ++first;
+  m = n - first;
+  if (m_out) *m_out = m;
+  if (k > m) { status = -3; goto out; }
+  X = (scalar*)malloc(sizeof(scalar) * (size_t)n * m);
+  for (int c = 0; c < m; ++c) {
+    const double f = 1.0 / sqrt(sig[first + c]);
+    for (int i = 0; i < n; ++i) AT(X, n, i, c) = f * AT(D, n, i, first + c);
+  }
+  /* 3. H~ = X^H H X */
+  HX = (scalar*)malloc(sizeof(scalar) * (size_t)n * m);
+#pragma omp parallel for schedule(static)
+  for (int c = 0; c < m; ++c)
+    for (int i = 0; i < n; ++i) {
+      scalar acc = 0;
+      for (int p = 0; p < n; ++p)
+        acc += ((i >= p) ? AT(H, ldh, i, p) : CONJ(AT(H, ldh, p, i))) * AT(X, n, p, c);
+      AT(HX, n, i, c) = acc;
+    }
+  Ht = (scalar*)malloc(sizeof(scalar) * (size_t)m * m);
+#pragma omp parallel for schedule(static)
+  for (int c = 0; c < m; ++c)
+    for (int r = 0; r < m; ++r) {
+      scalar acc = 0;
+      for (int i = 0; i < n; ++i) acc += CONJ(AT(X, n, i, r)) * AT(HX, n, i, c);
+      AT(Ht, m, r, c) = acc;
+    }
+  for (int c = 0; c < m; ++c)
+    for (int r = c; r < m; ++r) {
+      scalar h = 0.5 * (AT(Ht, m, r, c) + CONJ(AT(Ht, m, c, r)));
+      if (r == c) h = RE(h);
+      AT(Ht, m, r, c) = h;
+      AT(Ht, m, c, r) = CONJ(h);
+    }
+  /* 4. the reduced standard problem */
+  Yt = (scalar*)malloc(sizeof(scalar) * (size_t)m * m);
+  wt = (double*)malloc(sizeof(double) * m);
+  if (herm_eig(m, Ht, wt, Yt)) { status = -1; goto out; }
+  /* 5. C = X Y (the k lowest) */
+#pragma omp parallel for schedule(static)
+  for (int c = 0; c < k; ++c)
+    for (int i = 0; i < n; ++i) {
+      scalar acc = 0;
+      for (int r = 0; r < m; ++r) acc += AT(X, n, i, r) * AT(Yt, m, r, c);
+      AT(C, ldc, i, c) = acc;
+    }
+  for (int c = 0; c < k; ++c) w[c] = wt[c];
+  FN(normalize_phase)(n, k, C, ldc);
+out:
+  free(A); free(D); free(sig); free(X); free(HX); free(Ht); free(Yt); free(wt);
+  return status;
+}
+
+/* ---------------------------------------------------------------------------------------------
  * Density matrix of the computed orbitals (section "Circumventing the eigenvalue problem"):
  *   P_ij = sum_l  g_l conj(c_li) c_lj,
  * with c_li = C(i, l) the coefficient of basis function i in orbital l (column l of C).  The weights

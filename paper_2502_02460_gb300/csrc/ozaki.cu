@@ -32,10 +32,13 @@
 #include <cmath>
 
 #include "common.cuh"
+#include "tcgen05.cuh"
 
 namespace gev {
 
 namespace {
+
+using namespace tc;
 
 constexpr int OM = 128, ON = 64, KS = 16, NSTAGE = 4, NSLICE = 8, DMAX = 9, DEXACT = 7;
 constexpr int CHUNK = 32;                  // k-slices per exact chunk (512 of K)
@@ -55,65 +58,6 @@ constexpr int GROUP_M = 16;                // raster: 16 row tiles share their B
 constexpr int EXP_BAD = 1 << 20;           // exponent marking a non-finite entry
 constexpr int EXP_ZERO = -4000;            // exponent of an all-zero vector
 
-__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// byte offset of element (r, k) in a K-major 16-deep plane tile: 8 x 8 core matrices of 16-byte
-// rows, the two k-halves adjacent (leading offset 128 B), 8-row groups 256 B apart
-__host__ __device__ __forceinline__ int toff(int r, int k) {
-  return ((r >> 3) * 2 + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2;
-}
-
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
-  const uint64_t lbo = 128, sbo = 256;
-  return (uint64_t)((addr & 0x3FFFF) >> 4) | ((lbo >> 4) << 16) | ((sbo >> 4) << 32) | ((uint64_t)1 << 46);
-}
-
-// instruction descriptor: D = F32, A = B = BF16, both K-major, N = 64, M = 128
-__host__ __device__ constexpr uint32_t idesc_oz() {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(ON >> 3) << 17) | ((uint32_t)(OM >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, int acc) {
-  asm volatile(
-      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(id), "r"(acc));
-}
-
-__device__ __forceinline__ void commit(uint32_t mbar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar)
-               : "memory");
-}
-
-__device__ __forceinline__ bool try_wait(uint32_t mbar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(mbar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// bounded wait; gives up early once another role has recorded an error in *err
-__device__ __forceinline__ bool bar_wait(uint32_t mbar, uint32_t parity, volatile int* err) {
-  for (long long it = 0; it < kSpinLimit; ++it) {
-    if (try_wait(mbar, parity)) return true;
-    if ((it & 255) == 255 && *err) return false;
-    __nanosleep(32);
-  }
-  return false;
-}
-
-// bounded wait without the early exit (draining after an error)
-__device__ __forceinline__ bool bar_wait_plain(uint32_t mbar, uint32_t parity) {
-  for (long long it = 0; it < kSpinLimit; ++it) {
-    if (try_wait(mbar, parity)) return true;
-    __nanosleep(32);
-  }
-  return false;
-}
-
 // exponent e with |x| < 2^e for a finite x != 0; EXP_ZERO for 0, EXP_BAD for Inf / NaN
 __device__ __forceinline__ int exp_above(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
@@ -123,9 +67,6 @@ __device__ __forceinline__ int exp_above(double x) {
   return be - 1022;
 }
 
-__device__ __forceinline__ bool kept(int keep, long long r, long long k) {
-  return keep == 0 || (keep == 1 ? k <= r : k >= r);
-}
 
 // One operand of a product as the exponent and split passes see it: vectors r (rows of op(A) or
 // columns of op(B)) of elements k.  Real data: element (r, k) at X[r sr + k sk].  Complex data
@@ -227,7 +168,7 @@ __global__ void k_split(int R, int K, Opnd o, int fast_r, const int* E, int TR, 
   const long long rt = r / TR, kt = g >> 1;
   const int tile_bytes = TR * KS * 2;
   unsigned char* base =
-      out + ((rt * KT + kt) * NSLICE) * (long long)tile_bytes + toff((int)(r % TR), (int)(g & 1) * 8);
+      out + ((rt * KT + kt) * NSLICE) * (long long)tile_bytes + toff16((int)(r % TR), (int)(g & 1) * 8);
 #pragma unroll
   for (int p = 0; p < NSLICE; ++p) {
     uint4 v;
@@ -316,7 +257,7 @@ __global__ void k_split_bd(int M, BdOp o, int bm, int bk, int MT, int* E, unsign
 #pragma unroll
   for (int q = 0; q < 8; ++q) digits(v[q], Er, dg[q]);
   const int tile_bytes = OM * KS * 2;
-  unsigned char* base = out + (((long long)mt * c + (lane >> 1)) * NSLICE) * tile_bytes + toff((int)(i % OM), (lane & 1) * 8);
+  unsigned char* base = out + (((long long)mt * c + (lane >> 1)) * NSLICE) * tile_bytes + toff16((int)(i % OM), (lane & 1) * 8);
 #pragma unroll
   for (int p = 0; p < NSLICE; ++p) {
     uint4 w;
@@ -364,13 +305,6 @@ __device__ __forceinline__ double scale2(double x, int e) {
   return (x * pow2(h)) * pow2(e - h);
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-}
 
 __global__ void __launch_bounds__(NTH, 1) ozaki_kernel(OzP p) {
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -478,7 +412,7 @@ __global__ void __launch_bounds__(NTH, 1) ozaki_kernel(OzP p) {
   } else if (warp == NEPI_W + 1) {
     // ---- MMA warp: 36 digit-pair products per 16-deep slice
     if (lane == 0) {
-      const uint32_t id = idesc_oz();
+      const uint32_t id = idesc_bf16(OM, ON);
       for (int s = 0; s < nst; ++s) {
         const int slot = s % NSTAGE, c = s / CHUNK;
         const bool chunk_start = (s % CHUNK) == 0;
@@ -506,7 +440,7 @@ __global__ void __launch_bounds__(NTH, 1) ozaki_kernel(OzP p) {
               col = SHARED_SLOT * ON;
               en = (s == 0 && pa == 1 && qb == DEXACT) ? 0 : 1;
             }
-            mma(tmem + col, sdesc(a0 + (pa - 1) * A_TILE), sdesc(b0 + (qb - 1) * B_TILE), id, en);
+            mma_bf16(tmem + col, sdesc16(a0 + (pa - 1) * A_TILE), sdesc16(b0 + (qb - 1) * B_TILE), id, en);
           }
         }
         commit(su32(&empty[slot]));
