@@ -51,7 +51,8 @@ enum {
   GEV_ERR_OOM = 4,                   /* workspace allocation failed or exceeds workspace_limit */
   GEV_ERR_CUDA = 5,                  /* a CUDA runtime call failed */
   GEV_ERR_REUSE_WITHOUT_FACTOR = 6,  /* S == NULL but no resident factor is held */
-  GEV_ERR_UNSUPPORTED = 7            /* option combination not available */
+  GEV_ERR_UNSUPPORTED = 7,           /* option combination not available */
+  GEV_ERR_RANK = 9                   /* gev_solve_reduced: fewer than k eigenvalues of S reach delta */
 };
 
 /* Steps timed in gev_report.ms (milliseconds, CUDA events on the solve stream). */
@@ -141,6 +142,30 @@ int gev_setup(gev_sys** out, int n, int dtype, const gev_opts* opts);
    Synchronises the handle's stream before returning. */
 int gev_solve(gev_sys* s, const void* H, int ldh, const void* S, int lds, int k, double* evals,
               void* C, int ldc, gev_report* rep);
+
+/* Generalized solve for an ill-conditioned overlap (section "Current Status of the Implementation":
+   when S is numerically singular, the pencil is transformed to the basis of the eigenvectors D_i of S,
+   omitting every D_i whose eigenvalue sigma_i is smaller than a small positive delta, typically
+   delta <= 1e-5, as ELSI does).  On the device: S = D diag(sigma) D^H (all n pairs, by the same
+   two-stage chain as gev_solve), X = D_kept diag(sigma_kept)^{-1/2} (n x m, m = the number of
+   sigma_i >= delta), H~ = X^H H X (m x m), H~ Y = Y Lambda for the k lowest pairs, C = X Y.  C^H S C = I
+   on the kept space; C has no component along the omitted D_i.
+   H, S   : device, lower triangles read (ldh, lds >= n).  S may be NULL after gev_reuse_factor(s, 1)
+            and a successful reduced solve: the resident X of the last S is reused (not the factor
+            of gev_solve, and vice versa).
+   delta  : threshold on the eigenvalues of S, >= 0 and finite (delta = 0 also keeps zero
+            eigenvalues: use a positive delta for a singular S).
+   k      : 1 <= k <= n; evals (device, k doubles) ascending; C (device, n x k, ldc >= n).
+   m_kept : optional host int receiving m.  rep: optional host report (per-step times: the
+            eigendecomposition of S under "cholesky", H~ under "multiply", the reduced solve under
+            "to_band", C = X Y under "mult").
+   Runs the plain FP64 path whatever opts.prec says (the reduced problem is solved once per S in
+   FP64).  Returns 0, -i for an invalid i-th argument, GEV_ERR_RANK when m < k (nothing written to
+   evals / C), GEV_ERR_REUSE_WITHOUT_FACTOR, GEV_ERR_NO_CONVERGENCE, GEV_ERR_TIMEOUT, GEV_ERR_OOM (the
+   order-m handle of the reduced problem could not be allocated) or GEV_ERR_CUDA.  Synchronises the
+   handle's stream before returning. */
+int gev_solve_reduced(gev_sys* s, const void* H, int ldh, const void* S, int lds, double delta, int k,
+                      double* evals, void* C, int ldc, int* m_kept, gev_report* rep);
 
 /* Density matrix of k orbitals (section "Circumventing the eigenvalue problem") and, optionally,
    its energy-weighted counterpart (section "ELSI"):

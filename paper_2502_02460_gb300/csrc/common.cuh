@@ -290,6 +290,8 @@ struct Sys {
   int gemm_used = 0;
 
   bool have_factor = false;
+  int factor_kind = 0;    // resident factor: 0 = X = L^{-1} (Cholesky route), 1 = reduced basis (n x m)
+  int reduced_m = 0;      // kept basis size of the reduced route
   bool reuse = false;
   bool have_band = false;
   bool have_tridiag_refl = false;
@@ -377,6 +379,11 @@ inline int stop_on_timeout(Sys& s) {
   GEV_TRY(sync_status(s));
   return s.status_h[ST_TIMEOUT] ? GEV_ERR_TIMEOUT : 0;
 }
+Sys& sys_of(gev_sys* h);  // the handle's state (gev.cu)
+// ill-conditioned overlap: the reduced solve in the eigenbasis of S (reduced.cu)
+template <class T>
+int solve_reduced(Sys& s, const T* H, int ldh, const T* S, int lds, double delta, int k, double* evals, T* C,
+                  int ldc, int* m_kept, gev_report* rep);
 // gev_opts.check: residual and orthogonality of a solution, on the device (check.cu)
 template <class T>
 int measure(Sys& s, const T* H, int ldh, const T* S, int lds, int k, const double* evals, const T* C, int ldc,

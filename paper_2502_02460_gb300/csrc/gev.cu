@@ -137,6 +137,10 @@ template <class T> int solve_t(Sys& s, const T* H, int ldh, const T* S, int lds,
 
 }  // namespace
 
+namespace gev {
+Sys& sys_of(gev_sys* h) { return h->s; }
+}  // namespace gev
+
 extern "C" {
 
 void gev_default_opts(gev_opts* opts) {
@@ -153,6 +157,7 @@ const char* gev_strerror(int code) {
     case GEV_ERR_CUDA: return "CUDA runtime error";
     case GEV_ERR_REUSE_WITHOUT_FACTOR: return "S == NULL but no resident factor is held";
     case GEV_ERR_UNSUPPORTED: return "unsupported option combination";
+    case GEV_ERR_RANK: return "fewer than k eigenvalues of S reach delta";
     default: return code < 0 ? "invalid argument" : "unknown error";
   }
 }
@@ -245,7 +250,7 @@ int gev_solve(gev_sys* h, const void* H, int ldh, const void* S, int lds, int k,
   if (!evals) return -7;
   if (!C) return -8;
   if (ldc < n) return -9;
-  if (!S && !(s.reuse && s.have_factor)) return GEV_ERR_REUSE_WITHOUT_FACTOR;
+  if (!S && !(s.reuse && s.have_factor && s.factor_kind == 0)) return GEV_ERR_REUSE_WITHOUT_FACTOR;
   if (cudaSetDevice(s.opts.device) != cudaSuccess) return GEV_ERR_CUDA;
   if (rep) std::memset(rep, 0, sizeof(*rep));
   int r;
@@ -264,6 +269,43 @@ int gev_solve(gev_sys* h, const void* H, int ldh, const void* S, int lds, int k,
   }
   if (r == 0 && s.opts.check && S && rep) {
     // the accuracy of the returned pencil solution, on the device (two more products with C)
+    const int rc = s.dtype == GEV_C128
+                       ? measure<zd>(s, (const zd*)H, ldh, (const zd*)S, lds, k, evals, (const zd*)C, ldc,
+                                     &rep->resid, &rep->ortho)
+                       : measure<double>(s, (const double*)H, ldh, (const double*)S, lds, k, evals,
+                                         (const double*)C, ldc, &rep->resid, &rep->ortho);
+    if (rc) return rc;
+  }
+  return r;
+}
+
+int gev_solve_reduced(gev_sys* h, const void* H, int ldh, const void* S, int lds, double delta, int k,
+                      double* evals, void* C, int ldc, int* m_kept, gev_report* rep) {
+  if (!h) return -1;
+  Sys& s = h->s;
+  const int n = s.n;
+  if (!H) return -2;
+  if (ldh < n) return -3;
+  if (S && lds < n) return -5;
+  if (!(delta >= 0.0) || delta > 1e300) return -6;
+  if (k < 1 || k > n) return -7;
+  if (!evals) return -8;
+  if (!C) return -9;
+  if (ldc < n) return -10;
+  if (!S && !(s.reuse && s.have_factor && s.factor_kind == 1)) return GEV_ERR_REUSE_WITHOUT_FACTOR;
+  if (cudaSetDevice(s.opts.device) != cudaSuccess) return GEV_ERR_CUDA;
+  if (rep) std::memset(rep, 0, sizeof(*rep));
+  const int r = s.dtype == GEV_C128
+                    ? solve_reduced<zd>(s, (const zd*)H, ldh, (const zd*)S, lds, delta, k, evals, (zd*)C, ldc,
+                                        m_kept, rep)
+                    : solve_reduced<double>(s, (const double*)H, ldh, (const double*)S, lds, delta, k, evals,
+                                            (double*)C, ldc, m_kept, rep);
+  if (rep) {
+    rep->workspace_bytes = s.bytes;
+    rep->resid = -1.0;
+    rep->ortho = -1.0;
+  }
+  if (r == 0 && s.opts.check && S && rep) {
     const int rc = s.dtype == GEV_C128
                        ? measure<zd>(s, (const zd*)H, ldh, (const zd*)S, lds, k, evals, (const zd*)C, ldc,
                                      &rep->resid, &rep->ortho)
@@ -480,6 +522,7 @@ template <class T> int solve_t(Sys& s, const T* H, int ldh, const T* S, int lds,
   mark(GEV_STEP_MULTIPLY);
   GEV_TRY(hegst<T>(s, H, ldh, X, n, A, n));
   s.have_factor = true;
+  s.factor_kind = 0;
   // steps 4a / 4b: two-stage tridiagonalisation
   mark(GEV_STEP_TO_BAND);
   GEV_TRY(he2hb<T>(s, A, n, s.b));

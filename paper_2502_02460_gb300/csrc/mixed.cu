@@ -306,6 +306,7 @@ int solve_mixed(Sys& s, const double* H, int ldh, const double* S, int lds, int 
   mark(GEV_STEP_MULTIPLY);
   GEV_TRY(hegst<double>(s, H, ldh, X, n, A, n));
   s.have_factor = true;
+  s.factor_kind = 0;
   // ---- FP32 reduction of A32 = fl32(A); all n eigenvectors (the refinement uses the complement)
   mark(GEV_STEP_TO_BAND);
   float* A32 = (float*)s.W1;
@@ -520,6 +521,7 @@ int solve_mixed_cx(Sys& s, const zd* H, int ldh, const zd* S, int lds, int k, do
   mark(GEV_STEP_MULTIPLY);
   GEV_TRY(hegst<zd>(s, H, ldh, X, n, A, n));
   s.have_factor = true;
+  s.factor_kind = 0;
   // ---- full->band in FP64 on a copy of A (A stays for the refinement)
   mark(GEV_STEP_TO_BAND);
   zd* W1 = (zd*)s.W1;

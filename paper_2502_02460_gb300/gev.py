@@ -22,7 +22,7 @@ GEV_F64, GEV_C128 = 0, 1
 GEV_PLAIN, GEV_MIXED = 0, 1
 ERRORS = {
     1: "GEV_ERR_NOT_SPD", 2: "GEV_ERR_NO_CONVERGENCE", 3: "GEV_ERR_TIMEOUT", 4: "GEV_ERR_OOM",
-    5: "GEV_ERR_CUDA", 6: "GEV_ERR_REUSE_WITHOUT_FACTOR", 7: "GEV_ERR_UNSUPPORTED",
+    5: "GEV_ERR_CUDA", 6: "GEV_ERR_REUSE_WITHOUT_FACTOR", 7: "GEV_ERR_UNSUPPORTED", 9: "GEV_ERR_RANK",
 }
 STEP_NAMES = ["cholesky", "invert", "multiply", "to_band", "to_tridiag", "solve", "back_tridiag",
               "back_band", "mult", "refine"]
@@ -32,7 +32,7 @@ SYMBOLS = [
     "gev_default_opts", "gev_setup", "gev_solve", "gev_reuse_factor", "gev_free",
     "gev_workspace_bytes", "gev_strerror", "gev_step_potrf", "gev_step_trtri", "gev_step_hegst",
     "gev_step_he2hb", "gev_step_hb2st", "gev_step_stedc", "gev_step_back", "gev_step_mult",
-    "gev_density", "gev_check",
+    "gev_density", "gev_check", "gev_solve_reduced",
 ]
 
 
@@ -104,6 +104,7 @@ def lib() -> ctypes.CDLL:
         L.gev_density.argtypes = [vp, i, vp, i, vp, vp, vp, i, vp, i]
         dpp = ctypes.POINTER(ctypes.c_double)
         L.gev_check.argtypes = [vp, vp, i, vp, i, i, vp, vp, i, dpp, dpp]
+        L.gev_solve_reduced.argtypes = [vp, vp, i, vp, i, d, i, vp, vp, i, ip, ctypes.POINTER(Report)]
         for s in SYMBOLS:
             getattr(L, s).restype = getattr(L, s).restype or ctypes.c_int
         _lib = L
@@ -227,6 +228,25 @@ class Solver:
         self.last_report = rep.as_dict()
         _check(code, "gev_solve", rep.info)
         return evals, Cb
+
+    def solve_reduced_cm(self, Hb, Sb, delta: float, k: int, evals=None, Cb=None):
+        """Ill-conditioned overlap: the k lowest pairs in the eigenbasis of S with eigenvalues >= delta
+        (S may be None after ``reuse_factor(True)``).  Returns (evals, C, m) with m the kept basis size."""
+        import torch
+
+        n = self.n
+        if evals is None:
+            evals = torch.empty(k, dtype=torch.float64, device=self.device)
+        if Cb is None:
+            Cb = self._empty(n, k)
+        rep = Report()
+        m = ctypes.c_int(0)
+        code = lib().gev_solve_reduced(self.h, _ptr(Hb), n, _ptr(Sb), n, float(delta), k, _ptr(evals), _ptr(Cb), n,
+                                       ctypes.byref(m), ctypes.byref(rep))
+        self.last_report = rep.as_dict()
+        self.last_report["m_kept"] = m.value
+        _check(code, "gev_solve_reduced", m.value if code == 9 else 0)
+        return evals, Cb, m.value
 
     def solve(self, H, S, k: int):
         """Logical torch matrices (n x n) in, (eigenvalues[k], C[n x k]) out."""

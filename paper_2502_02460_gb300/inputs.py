@@ -177,3 +177,26 @@ def glued_wilkinson(m: int, copies: int, glue: float):
     for c in range(1, copies):
         e[c * m - 1] = glue
     return d, e
+
+
+def singular_overlap_pencil(n: int, m: int, complex_: bool, seed: int, dropped=(1e-9, 1e-12, 0.0)):
+    """A pencil with a numerically singular overlap: S = U diag(sigma) U^H with n - m eigenvalues from
+    ``dropped`` (below any usual threshold delta) and m drawn from U[0.1, 3];
+    H = U_m sigma_m^{1/2} Q diag(lambda) Q^H sigma_m^{1/2} U_m^H + U_d G U_d^H with lambda ~ U[-10, 5]
+    (sorted), Q Haar on the kept space and an arbitrary Hermitian G on the dropped directions.  In the
+    eigenbasis of S restricted to the kept directions the pencil's eigenvalues are exactly lambda.
+    Returns (H, S, lambda, U_d) as numpy arrays (Fortran order)."""
+    rng = np.random.default_rng(seed)
+    U, _ = np.linalg.qr(gaussian(n, rng, complex_))
+    sig = np.concatenate([np.resize(np.array(dropped, dtype=np.float64), n - m), rng.uniform(0.1, 3.0, m)])
+    S = (U * sig[None, :]) @ U.conj().T
+    S = 0.5 * (S + S.conj().T)
+    lam = np.sort(rng.uniform(-10.0, 5.0, m))
+    Q, _ = np.linalg.qr(gaussian(m, rng, complex_))
+    Um, Ud = U[:, n - m:], U[:, : n - m]
+    sh = np.sqrt(sig[n - m:])
+    Hm = (Um * sh[None, :]) @ ((Q * lam[None, :]) @ Q.conj().T) @ (Um * sh[None, :]).conj().T
+    Gd = gaussian(n - m, rng, complex_)
+    H = Hm + Ud @ (0.5 * (Gd + Gd.conj().T)) @ Ud.conj().T
+    H = 0.5 * (H + H.conj().T)
+    return np.asfortranarray(H), np.asfortranarray(S), lam, Ud

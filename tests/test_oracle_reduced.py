@@ -18,23 +18,8 @@ from paper_2502_02460_gb300 import inputs
 from tests.pins import jacobi_eig, norm1, real_embedding
 
 
-def constructed(n, m, cx, seed, dropped=(1e-9, 1e-12, 0.0)):
-    rng = np.random.default_rng(seed)
-    G = rng.standard_normal((n, n)) + (1j * rng.standard_normal((n, n)) if cx else 0)
-    U, _ = np.linalg.qr(G)
-    sig = np.concatenate([np.resize(np.array(dropped), n - m), rng.uniform(0.1, 3.0, m)])
-    S = (U * sig[None, :]) @ U.conj().T
-    S = 0.5 * (S + S.conj().T)
-    lam = np.sort(rng.uniform(-10.0, 5.0, m))
-    Gq = rng.standard_normal((m, m)) + (1j * rng.standard_normal((m, m)) if cx else 0)
-    Q, _ = np.linalg.qr(Gq)
-    Um, Ud = U[:, n - m:], U[:, : n - m]
-    sh = np.sqrt(sig[n - m:])
-    Hm = (Um * sh[None, :]) @ ((Q * lam[None, :]) @ Q.conj().T) @ (Um * sh[None, :]).conj().T
-    Gd = rng.standard_normal((n - m, n - m)) + (1j * rng.standard_normal((n - m, n - m)) if cx else 0)
-    H = Hm + Ud @ (0.5 * (Gd + Gd.conj().T)) @ Ud.conj().T
-    H = 0.5 * (H + H.conj().T)
-    return np.asfortranarray(H), np.asfortranarray(S), lam, Ud
+def constructed(n, m, cx, seed):
+    return inputs.singular_overlap_pencil(n, m, cx, seed)
 
 
 @pytest.mark.parametrize("cx", [False, True])
