@@ -168,6 +168,11 @@ class Solver:
         o.device = self.device.index
         o.cuda_stream = ctypes.c_void_p(self.stream.cuda_stream)
         o.prec = GEV_MIXED if mixed else GEV_PLAIN
+        if band_b == 0:  # the autotuner's table (tune.py) for this dtype, precision and order
+            from . import tune
+
+            band_b = tune.pick_band(n, complex_, mixed)
+        self.band_b = band_b
         o.band_b = band_b
         o.panel_nb = panel_nb
         o.timing = int(timing)
