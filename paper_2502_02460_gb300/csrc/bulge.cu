@@ -611,8 +611,12 @@ template <class T> int bt_levels_wy(Sys& s, int n, int k, int b, T* Y, int ldy) 
       if (!gemm_f32_bdiag(s, M1, k, rows, a1, b, 2 * b, Yl, ldy, 1.f, 0.f, P, M1)) return GEV_ERR_CUDA;
       if (!gemm_f32_bdiag(s, rows, k, M1, a2, 2 * b, b, P, M1, -1.f, 1.f, Yl, ldy)) return GEV_ERR_CUDA;
     } else {
-      if (!gemm_f64_bdiag(s, M1, k, rows, a1, b, 2 * b, Yl, ldy, 1.0, 0.0, P, M1)) return GEV_ERR_CUDA;
-      if (!gemm_f64_bdiag(s, rows, k, M1, a2, 2 * b, b, P, M1, -1.0, 1.0, Yl, ldy)) return GEV_ERR_CUDA;
+      // From orthonormal Z (s.z_unit), Y's columns stay unit vectors under the orthogonal transforms
+      // (|y_ij| <= 1), and |P_qj| = |v_q^H y_j| <= ||v_q|| <= sqrt(2) (a Householder vector with
+      // v(0) = 1): both below 2, so their scales need no pass over the data
+      const bool u = s.z_unit;
+      if (!gemm_f64_bdiag(s, M1, k, rows, a1, b, 2 * b, Yl, ldy, 1.0, 0.0, P, M1, u)) return GEV_ERR_CUDA;
+      if (!gemm_f64_bdiag(s, rows, k, M1, a2, 2 * b, b, P, M1, -1.0, 1.0, Yl, ldy, u)) return GEV_ERR_CUDA;
     }
   }
   return last_error();

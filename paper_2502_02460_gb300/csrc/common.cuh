@@ -203,10 +203,12 @@ struct BdOp {
 };
 // C (M x N) = alpha op(A) B + beta C, op(A) the block-diagonal operand (blocks bm x bk; M, K, bm, bk in
 // complex units for complex data), B (K x N, ld ldb) and C (ld ldc) as stored, on the emulated FP64
-// product engine; each output tile reads only its blocks' K range.  Returns false (nothing launched)
-// when s.ozws is too small: gemm_f64_bdiag_scratch gives the bytes.
+// product engine; each output tile reads only its blocks' K range.  b_below_two: the caller
+// guarantees every entry (real and imaginary part) of B is below 2 in magnitude, so the column
+// scales are fixed at 2 without a pass over B.  Returns false (nothing launched) when s.ozws is too
+// small: gemm_f64_bdiag_scratch gives the bytes.
 bool gemm_f64_bdiag(Sys& s, int M, int N, int K, const BdOp& a, int bm, int bk, const void* B, long long ldb,
-                    double alpha, double beta, void* C, long long ldc);
+                    double alpha, double beta, void* C, long long ldc, bool b_below_two);
 size_t gemm_f64_bdiag_scratch(int M, int N, int K, int bm, int bk, int cx);
 // The same in FP32 from BF16x6 (or x3, s.fp32_tc) split products on the tensor cores (tc_gemm.cu);
 // real data only.
@@ -292,6 +294,7 @@ struct Sys {
   bool have_factor = false;
   int factor_kind = 0;    // resident factor: 0 = X = L^{-1} (Cholesky route), 1 = reduced basis (n x m)
   int reduced_m = 0;      // kept basis size of the reduced route
+  bool z_unit = false;    // back-transform input: orthonormal columns (the divide-and-conquer output)
   bool reuse = false;
   bool have_band = false;
   bool have_tridiag_refl = false;

@@ -462,6 +462,7 @@ int gev_step_back(gev_sys* h, const double* Z, int ldz, int k, void* Y, int ldy)
   if (!Y) return -5;
   if (ldy < s.n) return -6;
   if (!s.have_band || !s.have_tridiag_refl) return GEV_ERR_UNSUPPORTED;
+  s.z_unit = false;  // the caller's Z: no bound on its entries is assumed
   int r = s.dtype == GEV_C128 ? back<zd>(s, Z, ldz, k, (zd*)Y, ldy) : back<double>(s, Z, ldz, k, (double*)Y, ldy);
   if (r) return r;
   GEV_CUDA_TRY(cudaStreamSynchronize(s.stream));
@@ -535,7 +536,9 @@ template <class T> int solve_t(Sys& s, const T* H, int ldh, const T* S, int lds,
   // step 6: Y = Q1 Q2 Z
   mark(GEV_STEP_BACK_TRIDIAG);
   T* Y = (T*)s.Yk;
+  s.z_unit = true;  // the divide-and-conquer eigenvectors
   GEV_TRY(bt_hb2st<T>(s, s.Zk, n, k, Y, n));
+  s.z_unit = false;
   mark(GEV_STEP_BACK_BAND);
   GEV_TRY(bt_he2hb<T>(s, Y, n, k));
   // step 7: C = X^H Y

@@ -322,7 +322,9 @@ int solve_mixed(Sys& s, const double* H, int ldh, const double* S, int lds, int 
   GEV_TRY(r);
   mark(GEV_STEP_BACK_TRIDIAG);
   float* Y32 = (float*)s.Yk;
+  s.z_unit = true;  // the divide-and-conquer eigenvectors
   GEV_TRY(bt_hb2st<float>(s, s.Zk, n, n, Y32, n));
+  s.z_unit = false;
   mark(GEV_STEP_BACK_BAND);
   GEV_TRY(bt_he2hb<float>(s, Y32, n, n));
   // ---- FP64 refinement of the k lowest pairs
@@ -544,7 +546,9 @@ int solve_mixed_cx(Sys& s, const zd* H, int ldh, const zd* S, int lds, int k, do
   GEV_TRY(r);
   mark(GEV_STEP_BACK_TRIDIAG);
   zf* Y32 = (zf*)s.Yk;
+  s.z_unit = true;  // the divide-and-conquer eigenvectors
   GEV_TRY(bt_hb2st<zf>(s, s.Zk, n, n, Y32, n));
+  s.z_unit = false;
   mark(GEV_STEP_BACK_BAND);
   zd* Vfull = W1;  // all n approximate eigenvectors in FP64
   GEV_TRY((convert2d<zf, zd>(s, n, n, Y32, n, Vfull, n)));

@@ -726,8 +726,14 @@ size_t gemm_f64_bdiag_scratch(int M, int N, int K, int bm, int bk, int cx) {
   return bd_layout(e * M, N, e * K, e * bm, e * bk).total;
 }
 
+namespace {
+__global__ void k_fill_exp(int n, int v, int* E) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) E[i] = v;
+}
+}  // namespace
+
 bool gemm_f64_bdiag(Sys& s, int M, int N, int K, const BdOp& a, int bm, int bk, const void* B, long long ldb,
-                    double alpha, double beta, void* C, long long ldc) {
+                    double alpha, double beta, void* C, long long ldc, bool b_below_two) {
   if (M <= 0 || N <= 0) return true;
   const int rs = a.cx ? 1 : 0;
   const int Me = M << rs, Ke = K << rs, bme = bm << rs, bke = bk << rs;
@@ -741,12 +747,19 @@ bool gemm_f64_bdiag(Sys& s, int M, int N, int K, const BdOp& a, int bm, int bk, 
   unsigned char* Bp = base + L.b_off;
   // op(B) column j, element k: B[k + j ldb] (complex: the re / im parts of element k / 2)
   const Opnd b{B, ldb, 1, 0, a.cx ? 2 : 0, 0, 0};
-  cudaMemsetAsync(F, 0x80, L.Np * sizeof(int), s.stream);
   GEV_COUNT(s);
   k_split_bd<<<cdiv((long long)L.MT * OM * 32, 256), 256, 0, s.stream>>>(Me, a, bme, bke, L.MT, E, Ap);
-  if (Ke > 0) {
+  if (b_below_two) {  // every entry of B below 2 in magnitude: the column exponents are 1, no pass over B
     GEV_COUNT(s);
-    k_vec_exp<<<dim3(cdiv(N, 8), cdiv(Ke, 1024)), dim3(32, 8), 0, s.stream>>>(N, Ke, b, 0, F);
+    k_fill_exp<<<cdiv(L.Np, 256), 256, 0, s.stream>>>((int)L.Np, 1, F);
+  } else {
+    cudaMemsetAsync(F, 0x80, L.Np * sizeof(int), s.stream);
+  }
+  if (Ke > 0) {
+    if (!b_below_two) {
+      GEV_COUNT(s);
+      k_vec_exp<<<dim3(cdiv(N, 8), cdiv(Ke, 1024)), dim3(32, 8), 0, s.stream>>>(N, Ke, b, 0, F);
+    }
     GEV_COUNT(s);
     k_split<<<cdiv((long long)L.NT * ON * 2 * L.KT, 256), 256, 0, s.stream>>>(N, Ke, b, 0, F, ON, L.NT, L.KT, Bp);
   }

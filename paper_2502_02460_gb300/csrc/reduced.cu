@@ -56,7 +56,9 @@ int solve_reduced(Sys& s, const T* H, int ldh, const T* S, int lds, double delta
     GEV_TRY(stop_on_timeout(s));
     GEV_TRY(stedc(s, s.d, s.e, n, s.w, s.Zk, n, nullptr));
     T* D = (T*)s.Yk;
+    s.z_unit = true;  // the divide-and-conquer eigenvectors
     GEV_TRY(back<T>(s, s.Zk, n, n, D, n));
+    s.z_unit = false;
     // 2. the kept basis
     std::vector<double> sig(n);
     GEV_CUDA_TRY(cudaMemcpyAsync(sig.data(), s.w, sizeof(double) * n, cudaMemcpyDeviceToHost, s.stream));
@@ -126,7 +128,9 @@ int solve_reduced(Sys& s, const T* H, int ldh, const T* S, int lds, double delta
   GEV_TRY(stop_on_timeout(u));
   GEV_TRY(stedc(u, u.d, u.e, k, u.w, u.Zk, m, nullptr));
   T* Yu = (T*)u.Yk;
+  u.z_unit = true;
   GEV_TRY(back<T>(u, u.Zk, m, k, Yu, m));
+  u.z_unit = false;
   GEV_TRY(sync_status(u));
   s.launches += u.launches;
   if (u.status_h[ST_TIMEOUT]) return GEV_ERR_TIMEOUT;
