@@ -248,6 +248,7 @@ struct Sys {
   size_t splitws_bytes = 0;
   void* band = nullptr;   // compact band, ldband x n
   void* bandtmp = nullptr;  // complex mixed form: FP64 copy of the band during its conversion
+  void* btg = nullptr;      // back-transform 1: T, Gram blocks and a block column of a 4-panel group (36 b^2)
   int ldband = 0;
   void* V2 = nullptr;     // bulge-chasing reflectors, b x (n * ntask)
   void* tau2 = nullptr;   // (n * ntask)

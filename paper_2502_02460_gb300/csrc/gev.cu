@@ -73,6 +73,8 @@ size_t carve(Sys& s, char* base) {
   size_t oR4 = L.add(mixed && s.dtype == GEV_C128 ? 3 * n * n * es : 8);
   // complex mixed form: staging copy of the FP64 band while it is converted to complex64
   size_t obt = L.add(mixed && s.dtype == GEV_C128 ? (size_t)ldband * (n + 2 * b) * es : 8);
+  // back-transform 1 groups of four panels: the group's T, Gram blocks and one block column
+  size_t obtg = L.add(36 * b * b * es);
   if (base) {
     s.A = base + oA; s.X = base + oX; s.W1 = base + oW1; s.V1 = base + oV1; s.T1 = base + oT1;
     s.dinv = base + odinv; s.Pn = base + oPn; s.small = base + osmall;
@@ -94,6 +96,7 @@ size_t carve(Sys& s, char* base) {
     s.R3 = (double*)(base + oR3);
     s.R4 = (double*)(base + oR4);
     s.bandtmp = base + obt;
+    s.btg = base + obtg;
   }
   return L.total;
 }

@@ -7,9 +7,12 @@
 //      (norm, then the reflector's inner products, which also give the column of the compact-WY
 //      factor T).  Q = H_0 ... H_{b-1} = I - Y T Y^H, T upper triangular.
 //   2. Two-sided update of the trailing block A22 <- Q^H A22 Q by GEMMs:
-//        W = A22 Y T,  U = T^H (Y^H W),  V = W - Y U / 2,  A22 -= Y V^H + V Y^H (lower), mirror.
+//        W = A22 Y T,  U = T^H (Y^H W),  V = W - Y U / 2,  A22 -= [Y V] [V Y]^H (lower, one
+//        rank-2b product), mirror.
 // Y is kept explicitly (unit diagonal, zeros above) in the handle's V1 at the panel's position and
 // T in T1, for the back-transform  Y_out = Q1 Z = Q_0 (Q_1 (... Q_last Z)).
+#include <algorithm>
+
 #include "common.cuh"
 #include "coop.cuh"
 
@@ -200,6 +203,9 @@ template <class T> int he2hb(Sys& s, T* A, int lda, int b) {
   const int n = s.n;
   GEV_TRY(allow_max_dyn_smem(k_panel_qr<T>));
   T* V1 = (T*)s.V1;
+  // the panels' reflector columns are stored from their own first row on; the rows above are zero so
+  // that consecutive panels form one wider compact-WY block in the back-transform
+  GEV_CUDA_TRY(cudaMemsetAsync(V1, 0, sizeof(T) * (size_t)n * n, s.stream));
   T* T1 = (T*)s.T1;
   T* W0 = (T*)s.Pn;
   T* W1 = W0 + (size_t)n * 2 * s.b;
@@ -237,21 +243,25 @@ template <class T> int he2hb(Sys& s, T* A, int lda, int b) {
     void* args[] = {&mm, &bb, &Pp, &ldp, &Yp, &ldy, &Tp, &nrm_part, &w_part, &alpha_g, &gb, &R, &use_smem};
     GEV_COUNT(s);
     GEV_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_panel_qr<T>, dim3(G), dim3(NT), args, smem, s.stream));
-    // ---- two-sided update of the trailing block
+    // ---- two-sided update of the trailing block, the rank-2b update as ONE product:
+    //      A22 -= Y V^H + V Y^H = [Y V] [V Y]^H  (K = 2b: the trailing block is read and written once)
     T* A22 = A + r0 + (long long)r0 * lda;
+    T* YV = W1;                                // m x 2b: [Y | V]
+    T* Wv = W1 + (size_t)n * b;                // its V half
+    T* VY = W0 + (size_t)2 * n * 2 * s.b;      // m x 2b: [V | Y] (third panel buffer)
     gemm(s, gp<T>(m, b, m, 0, 0, one, A22, lda, Yp, n, zero, W0, n));  // W0 = A22 Y
-    GemmP<T> g = gp<T>(m, b, b, 0, 0, one, W0, n, Tp, b, zero, W1, n);   // W = W0 T
+    GemmP<T> g = gp<T>(m, b, b, 0, 0, one, W0, n, Tp, b, zero, Wv, n);   // W = W0 T
     g.tri_b = 2;
     gemm(s, g);
-    gemm(s, gp<T>(b, b, m, 2, 0, one, Yp, n, W1, n, zero, sm0, b));    // Z = Y^H W
+    gemm(s, gp<T>(b, b, m, 2, 0, one, Yp, n, Wv, n, zero, sm0, b));    // Z = Y^H W
     g = gp<T>(b, b, b, 2, 0, one, Tp, b, sm0, b, zero, sm1, b);         // U = T^H Z
     g.tri_a = 1;
     gemm(s, g);
-    gemm(s, gp<T>(m, b, b, 0, 0, mhalf, Yp, n, sm1, b, one, W1, n));   // V = W - Y U / 2
-    g = gp<T>(m, m, b, 0, 2, mone, Yp, n, W1, n, one, A22, lda);        // A22 -= Y V^H
-    g.c_lower = 1;
-    gemm(s, g);
-    g = gp<T>(m, m, b, 0, 2, mone, W1, n, Yp, n, one, A22, lda);        // A22 -= V Y^H
+    gemm(s, gp<T>(m, b, b, 0, 0, mhalf, Yp, n, sm1, b, one, Wv, n));   // V = W - Y U / 2
+    GEV_TRY(copy2d<T>(s, m, b, Yp, n, YV, n));
+    GEV_TRY(copy2d<T>(s, m, b, Wv, n, VY, n));
+    GEV_TRY(copy2d<T>(s, m, b, Yp, n, VY + (size_t)n * b, n));
+    g = gp<T>(m, m, 2 * b, 0, 2, mone, YV, n, VY, n, one, A22, lda);    // A22 -= [Y V] [V Y]^H
     g.c_lower = 1;
     gemm(s, g);
     GEV_TRY(mirror_lower<T>(s, m, A22, lda));
@@ -274,24 +284,55 @@ template <class T> int he2hb(Sys& s, T* A, int lda, int b) {
   return 0;
 }
 
-// Y <- Q1 Y (n x k): apply the panels' compact-WY blocks, last panel first.
+// Y <- Q1 Y (n x k), Q1 = Q_0 Q_1 ... Q_last: the panels' compact-WY blocks, applied G panels at a
+// time.  Consecutive panels p .. p+G-1 merge into one block  Q_p ... Q_{p+G-1} = I - Yg Tg Yg^H  with
+// Yg = [Y_p ... Y_{p+G-1}] (the stored columns of V1 from row r0_p on: each Y_j is zero above its own
+// first row, V1 being cleared before the reduction) and Tg upper triangular, built block column by
+// block column from the panels' T_j and the Gram blocks Yg^H Yg:
+//     Tg(0:jb, jb:(j+1)b) = -Tg(0:jb, 0:jb) (Yg(:, 0:jb)^H Y_j) T_j,   Tg(jb.., jb..) = T_j.
+// Each group then costs three products with inner dimension G b (or m), applied last group first.
 template <class T> int bt_he2hb(Sys& s, T* Yb, int ldy, int k) {
   const int n = s.n, b = s.band_b_used;
   T* V1 = (T*)s.V1;
   T* T1 = (T*)s.T1;
-  T* Wk = (T*)s.Pn;                       // b x k
-  T* Wk2 = Wk + (size_t)n * 2 * s.b;      // b x k
+  const int np = s.nsbr_panels;
+  if (np <= 0) return 0;
+  const int G = std::min(4, np);
+  const int gb = G * b;                   // <= 4 b
+  T* Wk = (T*)s.Pn;                       // gb x k  (the panel buffers: 8 b n elements)
+  T* Wk2 = Wk + (size_t)gb * k;           // gb x k
+  T* Tg = (T*)s.btg;                      // gb x gb
+  T* Gg = Tg + (size_t)gb * gb;           // gb x gb Gram blocks
+  T* Xg = Gg + (size_t)gb * gb;           // gb x b
   const T one = from_re<T>(1.0), mone = from_re<T>(-1.0), zero = zero_<T>();
-  for (int p = s.nsbr_panels - 1; p >= 0; --p) {
-    const int j0 = p * b, r0 = j0 + b, m = n - r0;
-    const T* Yp = V1 + r0 + (long long)j0 * n;
-    const T* Tp = T1 + (long long)j0 * b;
+  const int ngroups = (np + G - 1) / G;
+  for (int q = ngroups - 1; q >= 0; --q) {
+    const int p0 = q * G, pc = std::min(G, np - p0), w = pc * b;
+    const int j0 = p0 * b, r0 = j0 + b, m = n - r0;
+    const T* Yg = V1 + r0 + (long long)j0 * n;  // m x w
+    // Tg: block column 0 = T_p0; block column j from the Gram blocks
+    GEV_CUDA_TRY(cudaMemset2DAsync(Tg, sizeof(T) * gb, 0, sizeof(T) * w, w, s.stream));
+    GEV_TRY(copy2d<T>(s, b, b, T1 + (long long)j0 * b, b, Tg, gb));
+    if (pc > 1) {
+      GemmP<T> g = gp<T>(w, w, m, 2, 0, one, Yg, n, Yg, n, zero, Gg, gb);  // Gram Yg^H Yg
+      gemm(s, g);
+      for (int j = 1; j < pc; ++j) {
+        const T* Tj = T1 + (long long)(j0 + j * b) * b;
+        g = gp<T>(j * b, b, b, 0, 0, one, Gg + (size_t)j * b * gb, gb, Tj, b, zero, Xg, gb);  // X = G(0:jb, j) T_j
+        g.tri_b = 2;
+        gemm(s, g);
+        g = gp<T>(j * b, b, j * b, 0, 0, mone, Tg, gb, Xg, gb, zero, Tg + (size_t)j * b * gb, gb);
+        g.tri_a = 2;                                                   // Tg(0:jb, j) = -Tg(0:jb, 0:jb) X
+        gemm(s, g);
+        GEV_TRY(copy2d<T>(s, b, b, Tj, b, Tg + j * b + (size_t)j * b * gb, gb));
+      }
+    }
     T* Ysub = Yb + r0;
-    gemm(s, gp<T>(b, k, m, 2, 0, one, Yp, n, Ysub, ldy, zero, Wk, b));
-    GemmP<T> g = gp<T>(b, k, b, 0, 0, one, Tp, b, Wk, b, zero, Wk2, b);
+    gemm(s, gp<T>(w, k, m, 2, 0, one, Yg, n, Ysub, ldy, zero, Wk, gb));  // Wk = Yg^H Y
+    GemmP<T> g = gp<T>(w, k, w, 0, 0, one, Tg, gb, Wk, gb, zero, Wk2, gb);  // Wk2 = Tg Wk
     g.tri_a = 2;
     gemm(s, g);
-    gemm(s, gp<T>(m, k, b, 0, 0, mone, Yp, n, Wk2, b, one, Ysub, ldy));
+    gemm(s, gp<T>(m, k, w, 0, 0, mone, Yg, n, Wk2, gb, one, Ysub, ldy));  // Y -= Yg Wk2
   }
   return last_error();
 }
