@@ -63,10 +63,13 @@ size_t carve(Sys& s, char* base) {
   size_t opanel = L.add(panel);
   size_t ost = L.add(sizeof(int) * ST_COUNT);
   size_t ozb = 0;
+  // inner dimensions reach max(n, 4b): the full->band rank-2b update and the back-transform-1 groups of
+  // four panels have K = 2b and 4b, which exceed n for small orders
+  const int kmax = std::max((int)n, 4 * (int)b);
   if (s.emu_fp64)  // complex products run in the real embedding: (2n x 2n) (2n x n)
-    ozb = s.dtype == GEV_C128 ? gemm_f64_emulated_scratch(2 * (int)n, (int)n, 2 * (int)n)
-                              : gemm_f64_emulated_scratch((int)n, (int)n, (int)n);
-  if (s.fp32_tc) ozb = std::max(ozb, gemm_tc32_scratch((int)n, (int)n, (int)n));
+    ozb = s.dtype == GEV_C128 ? gemm_f64_emulated_scratch(2 * (int)n, (int)n, 2 * kmax)
+                              : gemm_f64_emulated_scratch((int)n, (int)n, kmax);
+  if (s.fp32_tc) ozb = std::max(ozb, gemm_tc32_scratch((int)n, (int)n, kmax));
   size_t ooz = L.add(ozb);
   const bool mixed = s.opts.prec == GEV_MIXED;
   size_t oR1 = L.add(mixed ? n * n * es : 8), oR2 = L.add(mixed ? n * n * es : 8), oR3 = L.add(mixed ? n * n * es : 8);
