@@ -354,6 +354,74 @@ def run_stream_only(args):
     return 0
 
 
+CONFIGS = [  # (name, n, k, seed, complex, cluster)
+    ("config 0: real N=512, all pairs, seed 0", 512, 512, 0, False, False),
+    ("config 1: real N=4096, k=1229, seed 1, 1e-8 cluster of 16", 4096, 1229, 1, False, True),
+    ("config 2: complex128 N=20000, k=5000, seed 2", 20000, 5000, 2, True, False),
+]
+
+
+def run_configs(args):
+    """The smaller configurations timed on the GPU (plain FP64 with emulated and native products, and
+    the mixed form): median of ``--steps`` solves after ``--warmup``, CUDA events on the solve
+    stream, inputs resident; eigenvalue error against the construction and the on-device
+    residual / orthogonality of one more solve."""
+    import numpy as np
+    import torch
+
+    from paper_2502_02460_gb300 import build, gev, inputs
+
+    build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    out = []
+    for name, n, k, seed, cx, cluster in CONFIGS:
+        if args.configs_max_n and n > args.configs_max_n:
+            continue
+        on_gpu = n > 4096
+        p = inputs.make_problem(n, k, seed=seed, complex_=cx, cluster=cluster, device=dev if on_gpu else None,
+                                gap_check=not on_gpu)
+        Hb, Sb = (p.H, p.S) if on_gpu else (gev.cm_from_numpy(p.H, dev), gev.cm_from_numpy(p.S, dev))
+        h1 = float(Hb.abs().sum(dim=1).max().item())
+        rows = {}
+        forms = [("plain_emulated", False, 1), ("mixed", True, -1)]
+        if n <= 4096:
+            forms.insert(1, ("plain_native", False, 0))
+        for form, mixed, emu in forms:
+            with gev.Solver(n, complex_=cx, device=dev, mixed=mixed, fp64_emulation=emu, timing=1, stream=stream,
+                            check=True) as sv:
+                w = torch.empty(k, dtype=torch.float64, device=dev)
+                Cb = torch.empty((k, n), dtype=sv.dtype, device=dev)
+                sv.solve_cm(Hb, Sb, k, w, Cb)
+                acc = {"resid": sv.last_report["resid"], "ortho": sv.last_report["ortho"]}
+                sv.opts.check = 0
+            with gev.Solver(n, complex_=cx, device=dev, mixed=mixed, fp64_emulation=emu, timing=1,
+                            stream=stream) as sv:
+                for _ in range(args.warmup):
+                    sv.solve_cm(Hb, Sb, k, w, Cb)
+                times, steps = [], []
+                for _ in range(args.steps):
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    sv.solve_cm(Hb, Sb, k, w, Cb)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    times.append(e0.elapsed_time(e1) / 1e3)
+                    steps.append(sv.last_report["ms"])
+            err = float(np.max(np.abs(w.cpu().numpy() - p.lam[:k])))
+            rows[form] = {"s": statistics.median(times), "per_step_s": times,
+                          "steps_ms": {kk: statistics.median(r[kk] for r in steps) for kk in gev.STEP_NAMES},
+                          "max_abs_eig_err_vs_construction": err, "err_over_h1": err / h1, **acc}
+        out.append({"config": name, "n": n, "k": k, "complex": cx, "h1": h1, "forms": rows,
+                    "steps": args.steps, "warmup": args.warmup})
+        del Hb, Sb, p
+        torch.cuda.empty_cache()
+    print(json.dumps({"metric": "time-to-solution of configurations 0-2 (s)", "configs": out}), flush=True)
+    return 0
+
+
 def time_density(solver, Cb, w, Sb, dev, stream, reps=5, warmup=3):
     """Density matrix and energy-weighted density matrix (gev_density) of the benchmarked orbitals,
     every orbital doubly occupied; CUDA events on the solver's stream around ``reps`` calls."""
@@ -416,6 +484,10 @@ def main():
     ap.add_argument("--stream-n-max", type=int, default=2048)
     ap.add_argument("--stream-full", action="store_true",
                     help="the whole k-point stream: 512 requests, N log-uniform in [256, 8192]")
+    ap.add_argument("--configs", action="store_true",
+                    help="time configurations 0-2 (N=512 all pairs; N=4096 k=1229 cluster; complex N=20000 "
+                         "k=5000) in every form and print one line")
+    ap.add_argument("--configs-max-n", type=int, default=0, help="--configs: skip orders above this (0 = none)")
     ap.add_argument("--stream-only", action="store_true",
                     help="run only the k-point stream (both precisions) and print its line")
     ap.add_argument("--band-b", type=int, default=64)
@@ -441,6 +513,8 @@ def main():
         return run_reference(args)
     if args.stream_only:
         return run_stream_only(args)
+    if args.configs:
+        return run_configs(args)
 
     import torch
 
