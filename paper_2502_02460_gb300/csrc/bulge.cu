@@ -356,15 +356,17 @@ __global__ void __launch_bounds__(COLS) k_bt_bulge_level(int n, int k, int b, in
   }
 }
 
-// FP32 form of the level kernel: the same (group, task) blocks and level order, but each thread
-// applies the reflectors to its column from registers.  The 64 reflectors of a block are taken in
-// chunks of 8 (descending): a chunk touches window rows [q0, q0 + B + 7), which are moved from the
-// staged shared-memory window into registers, updated by the 8 reflectors (dot products with four
-// partial sums) and written back.  Reflector entries are shared-memory broadcasts, zero-padded
-// beyond the matrix end, so every chunk runs the same straight-line code.
+// FP32 form of the level kernel: the same (group, task) blocks and level order, each thread applying
+// the block's reflectors to its own column from registers.  The reflectors are taken in chunks of 8
+// (descending); chunk q0 touches window rows [q0, q0 + B + 7).  The thread keeps those B + 7 rows in
+// registers and slides them up by 8 rows per chunk: the bottom 8 (final for this block) are stored,
+// the others move down, and 8 new rows are loaded from global memory (scalar loads; a warp's
+// 32 columns are 32 cache sectors that the next 7 rows hit in L1).  Only the reflector block and its
+// tau are staged in shared memory (broadcast reads; zero-padded beyond the matrix end, so every
+// chunk runs the same straight-line code), which keeps several CTAs per SM to hide the loads.
 constexpr int BTF_COLS = 128, BTF_CH = 8;
 template <int B>
-__global__ void __launch_bounds__(BTF_COLS) k_bt_level_f32(int n, int k, int L, int ngroups, const float* V2,
+__global__ void __launch_bounds__(BTF_COLS, 3) k_bt_level_f32(int n, int k, int L, int ngroups, const float* V2,
                                                            const float* tau2, int ntask, float* Y, long long ldy) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int g = max(0, ngroups - 1 - L) + blockIdx.x;
@@ -375,12 +377,9 @@ __global__ void __launch_bounds__(BTF_COLS) k_bt_level_f32(int n, int k, int L, 
   const int w0 = s0 + 1 + t * B;
   if (w0 >= n) return;
   const int rows = min(n, s1 + 1 + t * B + B) - w0;  // <= 2B - 1
-  constexpr int LDZ = BTF_COLS + 1;
-  float* Zs = reinterpret_cast<float*>(smraw);          // 2B x LDZ
-  float* Vs = Zs + 2 * B * LDZ;                          // B x B (16-byte aligned rows)
-  float* ts = Vs + B * B;                                // B
-  const int c0 = blockIdx.y * BTF_COLS;
-  const int ncols = min(BTF_COLS, k - c0);
+  float* Vs = reinterpret_cast<float*>(smraw);       // B x B (16-byte aligned rows)
+  float* ts = Vs + B * B;                             // B
+  const int c = blockIdx.y * BTF_COLS + threadIdx.x;
   for (int idx = threadIdx.x; idx < B * B; idx += BTF_COLS) {
     const int q = idx / B, i = idx % B;
     const int p = s0 + q + 1 + t * B;
@@ -389,18 +388,31 @@ __global__ void __launch_bounds__(BTF_COLS) k_bt_level_f32(int n, int k, int L, 
     Vs[idx] = v;
   }
   for (int q = threadIdx.x; q < B; q += BTF_COLS) ts[q] = (s0 + q <= s1) ? tau2[(long long)(s0 + q) * ntask + t] : 0.f;
-  for (int idx = threadIdx.x; idx < 2 * B * BTF_COLS; idx += BTF_COLS) {
-    const int r = idx % (2 * B), c = idx / (2 * B);  // consecutive threads: consecutive rows
-    float v = 0.f;
-    if (r < rows && c < ncols) v = Y[(w0 + r) + (long long)(c0 + c) * ldy];
-    Zs[r * LDZ + c] = v;
-  }
   __syncthreads();
-  const int c = threadIdx.x;
-  for (int q0 = B - BTF_CH; q0 >= 0; q0 -= BTF_CH) {
-    float z[B + BTF_CH - 1];
+  if (c >= k) return;
+  float* col = Y + w0 + (long long)c * ldy;  // window row r of this column: col[r], r < rows
+  constexpr int NZ = B + BTF_CH - 1;
+  float z[NZ];
+  // first chunk q0 = B - 8: rows B - 8 .. 2B - 2
 #pragma unroll
-    for (int j = 0; j < B + BTF_CH - 1; ++j) z[j] = Zs[(q0 + j) * LDZ + c];
+  for (int j = 0; j < NZ; ++j) {
+    const int r = B - BTF_CH + j;
+    z[j] = (r < rows) ? col[r] : 0.f;
+  }
+  for (int q0 = B - BTF_CH; q0 >= 0; q0 -= BTF_CH) {
+    if (q0 < B - BTF_CH) {
+      // slide: the previous chunk (q0 + 8) held rows q0 + 8 .. q0 + 8 + NZ - 1; its last 8,
+      // rows q0 + NZ .. q0 + NZ + 7 (z[NZ-8 .. NZ-1]), are final; the rest move down by 8
+#pragma unroll
+      for (int j = 0; j < BTF_CH; ++j) {
+        const int r = q0 + NZ + j;
+        if (r < rows) col[r] = z[NZ - BTF_CH + j];
+      }
+#pragma unroll
+      for (int j = NZ - 1; j >= BTF_CH; --j) z[j] = z[j - BTF_CH];
+#pragma unroll
+      for (int j = 0; j < BTF_CH; ++j) z[j] = (q0 + j < rows) ? col[q0 + j] : 0.f;
+    }
 #pragma unroll
     for (int u = BTF_CH - 1; u >= 0; --u) {
       const float4* v4 = reinterpret_cast<const float4*>(Vs + (q0 + u) * B);
@@ -423,14 +435,11 @@ __global__ void __launch_bounds__(BTF_COLS) k_bt_level_f32(int n, int k, int L, 
         z[u + 4 * i + 3] = fmaf(-v.w, w, z[u + 4 * i + 3]);
       }
     }
+  }
+  // chunk 0 leaves rows 0 .. B + 6 in z
 #pragma unroll
-    for (int j = 0; j < B + BTF_CH - 1; ++j) Zs[(q0 + j) * LDZ + c] = z[j];
-  }
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < 2 * B * BTF_COLS; idx += BTF_COLS) {
-    const int r = idx % (2 * B), cc = idx / (2 * B);
-    if (r < rows && cc < ncols) Y[(w0 + r) + (long long)(c0 + cc) * ldy] = Zs[r * LDZ + cc];
-  }
+  for (int j = 0; j < NZ; ++j)
+    if (j < rows) col[j] = z[j];
 }
 
 // Compact-WY form of one level's reflector blocks, for the tensor-core back-transform: for block j
@@ -439,18 +448,19 @@ __global__ void __launch_bounds__(BTF_COLS) k_bt_level_f32(int n, int k, int L, 
 //   D_j = H(s0) H(s0 + 1) ... H(s0 + b - 1) = I - V T V^H,  T upper triangular:
 //   T_qq = tau_q,  T(0:q, q) = -tau_q T(0:q, 0:q) (V(:, 0:q)^H v_q),
 // and W_j = V T (2b x b, column-major at W + j 2b b) is written for the second product.  A reflector
-// with tau = 0 (a task that never ran) is a zero column.  One block of 256 threads per D_j.
+// with tau = 0 (a task that never ran) is a zero column.  One block of 256 threads per D_j: the Gram
+// entries V^H V by all threads (padded shared-memory columns), the recurrence by one warp, W by all.
 template <class T>
 __global__ void __launch_bounds__(256) k_wy_level(int n, int b, int L, int ngroups, int g_lo, int w00, int ntask,
                                                   const T* V2, const T* tau2, T* W) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int j = blockIdx.x, tid = threadIdx.x;
   const int g = g_lo + j, t = L - (ngroups - 1 - g);
-  const int m = 2 * b;
-  T* Vs = reinterpret_cast<T*>(smraw);  // 2b x b
-  T* Ts = Vs + (size_t)m * b;           // b x b
-  T* z = Ts + (size_t)b * b;            // b
-  T* taus = z + b;                      // b
+  const int m = 2 * b, ldv = m + 1;     // padded: column q of V starts q (2b + 1) elements in
+  T* Vs = reinterpret_cast<T*>(smraw);  // 2b x b (ld 2b + 1)
+  T* Gs = Vs + (size_t)ldv * b;         // b x b Gram V^H V, then overwritten by T (strict upper part)
+  T* taus = Gs + (size_t)b * (b + 1);   // b
+  const int ldg = b + 1;
   const int w0 = w00 + m * j;
   for (int idx = tid; idx < m * b; idx += blockDim.x) {
     const int r = idx % m, q = idx / m;
@@ -460,38 +470,54 @@ __global__ void __launch_bounds__(256) k_wy_level(int n, int b, int L, int ngrou
       const long long rid = (long long)sw * ntask + t;
       if (tau2[rid] != zero_<T>()) v = V2[rid * b + rel];
     }
-    Vs[idx] = v;
+    Vs[r + q * ldv] = v;
   }
   for (int q = tid; q < b; q += blockDim.x) {
     const int sw = g * b + q;
     taus[q] = (sw <= n - 3) ? tau2[(long long)sw * ntask + t] : zero_<T>();
   }
-  for (int idx = tid; idx < b * b; idx += blockDim.x) Ts[idx] = zero_<T>();
   __syncthreads();
-  for (int q = 0; q < b; ++q) {
-    // z_p = v_p^H v_q for p < q (overlap rows q .. p + b - 1)
-    for (int p = tid; p < q; p += blockDim.x) {
+  // Gram entries G(p, q) = v_p^H v_q, p < q (rows q .. p + b - 1 overlap)
+  for (int idx = tid; idx < b * b; idx += blockDim.x) {
+    const int p = idx % b, q = idx / b;
+    if (p < q) {
       T acc = zero_<T>();
-      for (int r = q; r < p + b; ++r) acc += cmul(Vs[r + p * m], Vs[r + q * m]);
-      z[p] = acc;
+      for (int r = q; r < p + b; ++r) acc += cmul(Vs[r + p * ldv], Vs[r + q * ldv]);
+      Gs[p + q * ldg] = acc;
     }
-    __syncthreads();
-    const T tq = taus[q];
-    for (int p = tid; p < q; p += blockDim.x) {
-      T acc = zero_<T>();
-      for (int l = p; l < q; ++l) acc += Ts[p + l * b] * z[l];
-      Ts[p + q * b] = -(tq * acc);
-    }
-    if (tid == 0) Ts[q + q * b] = tq;
-    __syncthreads();
   }
-  // W = V T: W(r, q) = sum_{p <= q} V(r, p) T(p, q), V(r, p) != 0 for r - b < p <= r
+  __syncthreads();
+  // T by columns, in place over the Gram matrix's strict upper part: column q needs G(0:q, q) and the
+  // finished columns 0 .. q-1 of T (diagonal: tau); one warp, two entries per lane (b <= 64)
+  if (tid < 32) {
+    for (int q = 0; q < b; ++q) {
+      const T tq = taus[q];
+      T out[2];
+      for (int h = 0; h < 2; ++h) {
+        const int p = tid + 32 * h;
+        out[h] = zero_<T>();
+        if (p < q) {
+          T acc = zero_<T>();
+          for (int l = p; l < q; ++l) acc += ((l == p) ? taus[p] : Gs[p + l * ldg]) * Gs[l + q * ldg];
+          out[h] = -(tq * acc);
+        }
+      }
+      __syncwarp();
+      for (int h = 0; h < 2; ++h) {
+        const int p = tid + 32 * h;
+        if (p < q) Gs[p + q * ldg] = out[h];
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  // W = V T: W(r, q) = sum_{p <= q} V(r, p) T(p, q), V(r, p) != 0 for r - b < p <= r (T_pp = tau_p)
   T* Wj = W + (size_t)j * m * b;
   for (int idx = tid; idx < m * b; idx += blockDim.x) {
     const int r = idx % m, q = idx / m;
     const int p0 = max(0, r - b + 1), p1 = min(q, r);
     T acc = zero_<T>();
-    for (int p = p0; p <= p1; ++p) acc += Vs[r + p * m] * Ts[p + q * b];
+    for (int p = p0; p <= p1; ++p) acc += Vs[r + p * ldv] * ((p == q) ? taus[q] : Gs[p + q * ldg]);
     Wj[idx] = acc;
   }
 }
@@ -594,7 +620,7 @@ template <class T> int bt_levels_wy(Sys& s, int n, int k, int b, T* Y, int ldy) 
   if (need > s.ozws_bytes || (size_t)max_nblk * b * k * sizeof(T) > (size_t)n * n * sizeof(T) ||
       (size_t)max_nblk * 2 * b * b * sizeof(T) > (size_t)n * n * sizeof(double))
     return GEV_ERR_UNSUPPORTED;
-  const size_t smem = sizeof(T) * ((size_t)2 * b * b + (size_t)b * b + 2 * b) + 64;
+  const size_t smem = sizeof(T) * ((size_t)(2 * b + 1) * b + (size_t)b * (b + 1) + b) + 64;
   GEV_TRY(allow_dyn_smem(k_wy_level<T>, smem));
   for (int L = 0; L < nlevels; ++L) {
     const LevelBlocks lb = level_blocks(n, b, L, ngroups, s.ntask);
@@ -624,7 +650,7 @@ template <class T> int bt_levels_wy(Sys& s, int n, int k, int b, T* Y, int ldy) 
 
 template <int B> int bt_levels_f32(Sys& s, int n, int k, float* Y, int ldy) {
   const int ngroups = (n - 3) / B + 1;
-  const size_t smem = sizeof(float) * ((size_t)2 * B * (BTF_COLS + 1) + (size_t)B * B + B) + 64;
+  const size_t smem = sizeof(float) * ((size_t)B * B + B) + 64;
   GEV_TRY(allow_max_dyn_smem(k_bt_level_f32<B>));
   const int nlevels = ngroups + s.ntask;
   const unsigned ycb = cdiv(k, BTF_COLS);
@@ -650,11 +676,8 @@ template <class T> int bt_hb2st(Sys& s, const double* Z, int ldz, int k, T* Y, i
   }
   if (n <= 2) return 0;
   if constexpr (std::is_same<T, float>::value) {
-    // mixed form with the FP32 tensor products: each level as two block-diagonal BF16x6 products
-    if (s.fp32_tc) {
-      const int r = bt_levels_wy<float>(s, n, k, b, Y, ldy);
-      if (r != GEV_ERR_UNSUPPORTED) return r;  // else: the scratch is too small, take the level kernel
-    }
+    // (the block-diagonal BF16x6 form, bt_levels_wy<float>, measured slower than this register kernel
+    // at n = 16384: 747 ms against 556 ms, its split passes and short-K products being latency bound)
     if (b == 16) return bt_levels_f32<16>(s, n, k, Y, ldy);
     if (b == 32) return bt_levels_f32<32>(s, n, k, Y, ldy);
     if (b == 64) return bt_levels_f32<64>(s, n, k, Y, ldy);
