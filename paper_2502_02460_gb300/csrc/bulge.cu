@@ -356,17 +356,15 @@ __global__ void __launch_bounds__(COLS) k_bt_bulge_level(int n, int k, int b, in
   }
 }
 
-// FP32 form of the level kernel: the same (group, task) blocks and level order, each thread applying
-// the block's reflectors to its own column from registers.  The reflectors are taken in chunks of 8
-// (descending); chunk q0 touches window rows [q0, q0 + B + 7).  The thread keeps those B + 7 rows in
-// registers and slides them up by 8 rows per chunk: the bottom 8 (final for this block) are stored,
-// the others move down, and 8 new rows are loaded from global memory (scalar loads; a warp's
-// 32 columns are 32 cache sectors that the next 7 rows hit in L1).  Only the reflector block and its
-// tau are staged in shared memory (broadcast reads; zero-padded beyond the matrix end, so every
-// chunk runs the same straight-line code), which keeps several CTAs per SM to hide the loads.
+// FP32 form of the level kernel: the same (group, task) blocks and level order, but each thread
+// applies the reflectors to its column from registers.  The 64 reflectors of a block are taken in
+// chunks of 8 (descending): a chunk touches window rows [q0, q0 + B + 7), which are moved from the
+// staged shared-memory window into registers, updated by the 8 reflectors (dot products with four
+// partial sums) and written back.  Reflector entries are shared-memory broadcasts, zero-padded
+// beyond the matrix end, so every chunk runs the same straight-line code.
 constexpr int BTF_COLS = 128, BTF_CH = 8;
 template <int B>
-__global__ void __launch_bounds__(BTF_COLS, 3) k_bt_level_f32(int n, int k, int L, int ngroups, const float* V2,
+__global__ void __launch_bounds__(BTF_COLS) k_bt_level_f32(int n, int k, int L, int ngroups, const float* V2,
                                                            const float* tau2, int ntask, float* Y, long long ldy) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int g = max(0, ngroups - 1 - L) + blockIdx.x;
@@ -377,9 +375,12 @@ __global__ void __launch_bounds__(BTF_COLS, 3) k_bt_level_f32(int n, int k, int 
   const int w0 = s0 + 1 + t * B;
   if (w0 >= n) return;
   const int rows = min(n, s1 + 1 + t * B + B) - w0;  // <= 2B - 1
-  float* Vs = reinterpret_cast<float*>(smraw);       // B x B (16-byte aligned rows)
-  float* ts = Vs + B * B;                             // B
-  const int c = blockIdx.y * BTF_COLS + threadIdx.x;
+  constexpr int LDZ = BTF_COLS + 1;
+  float* Zs = reinterpret_cast<float*>(smraw);          // 2B x LDZ
+  float* Vs = Zs + 2 * B * LDZ;                          // B x B (16-byte aligned rows)
+  float* ts = Vs + B * B;                                // B
+  const int c0 = blockIdx.y * BTF_COLS;
+  const int ncols = min(BTF_COLS, k - c0);
   for (int idx = threadIdx.x; idx < B * B; idx += BTF_COLS) {
     const int q = idx / B, i = idx % B;
     const int p = s0 + q + 1 + t * B;
@@ -388,31 +389,18 @@ __global__ void __launch_bounds__(BTF_COLS, 3) k_bt_level_f32(int n, int k, int 
     Vs[idx] = v;
   }
   for (int q = threadIdx.x; q < B; q += BTF_COLS) ts[q] = (s0 + q <= s1) ? tau2[(long long)(s0 + q) * ntask + t] : 0.f;
-  __syncthreads();
-  if (c >= k) return;
-  float* col = Y + w0 + (long long)c * ldy;  // window row r of this column: col[r], r < rows
-  constexpr int NZ = B + BTF_CH - 1;
-  float z[NZ];
-  // first chunk q0 = B - 8: rows B - 8 .. 2B - 2
-#pragma unroll
-  for (int j = 0; j < NZ; ++j) {
-    const int r = B - BTF_CH + j;
-    z[j] = (r < rows) ? col[r] : 0.f;
+  for (int idx = threadIdx.x; idx < 2 * B * BTF_COLS; idx += BTF_COLS) {
+    const int r = idx % (2 * B), c = idx / (2 * B);  // consecutive threads: consecutive rows
+    float v = 0.f;
+    if (r < rows && c < ncols) v = Y[(w0 + r) + (long long)(c0 + c) * ldy];
+    Zs[r * LDZ + c] = v;
   }
+  __syncthreads();
+  const int c = threadIdx.x;
   for (int q0 = B - BTF_CH; q0 >= 0; q0 -= BTF_CH) {
-    if (q0 < B - BTF_CH) {
-      // slide: the previous chunk (q0 + 8) held rows q0 + 8 .. q0 + 8 + NZ - 1; its last 8,
-      // rows q0 + NZ .. q0 + NZ + 7 (z[NZ-8 .. NZ-1]), are final; the rest move down by 8
+    float z[B + BTF_CH - 1];
 #pragma unroll
-      for (int j = 0; j < BTF_CH; ++j) {
-        const int r = q0 + NZ + j;
-        if (r < rows) col[r] = z[NZ - BTF_CH + j];
-      }
-#pragma unroll
-      for (int j = NZ - 1; j >= BTF_CH; --j) z[j] = z[j - BTF_CH];
-#pragma unroll
-      for (int j = 0; j < BTF_CH; ++j) z[j] = (q0 + j < rows) ? col[q0 + j] : 0.f;
-    }
+    for (int j = 0; j < B + BTF_CH - 1; ++j) z[j] = Zs[(q0 + j) * LDZ + c];
 #pragma unroll
     for (int u = BTF_CH - 1; u >= 0; --u) {
       const float4* v4 = reinterpret_cast<const float4*>(Vs + (q0 + u) * B);
@@ -435,11 +423,14 @@ __global__ void __launch_bounds__(BTF_COLS, 3) k_bt_level_f32(int n, int k, int 
         z[u + 4 * i + 3] = fmaf(-v.w, w, z[u + 4 * i + 3]);
       }
     }
-  }
-  // chunk 0 leaves rows 0 .. B + 6 in z
 #pragma unroll
-  for (int j = 0; j < NZ; ++j)
-    if (j < rows) col[j] = z[j];
+    for (int j = 0; j < B + BTF_CH - 1; ++j) Zs[(q0 + j) * LDZ + c] = z[j];
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < 2 * B * BTF_COLS; idx += BTF_COLS) {
+    const int r = idx % (2 * B), cc = idx / (2 * B);
+    if (r < rows && cc < ncols) Y[(w0 + r) + (long long)(c0 + cc) * ldy] = Zs[r * LDZ + cc];
+  }
 }
 
 // Compact-WY form of one level's reflector blocks, for the tensor-core back-transform: for block j
@@ -650,7 +641,7 @@ template <class T> int bt_levels_wy(Sys& s, int n, int k, int b, T* Y, int ldy) 
 
 template <int B> int bt_levels_f32(Sys& s, int n, int k, float* Y, int ldy) {
   const int ngroups = (n - 3) / B + 1;
-  const size_t smem = sizeof(float) * ((size_t)B * B + B) + 64;
+  const size_t smem = sizeof(float) * ((size_t)2 * B * (BTF_COLS + 1) + (size_t)B * B + B) + 64;
   GEV_TRY(allow_max_dyn_smem(k_bt_level_f32<B>));
   const int nlevels = ngroups + s.ntask;
   const unsigned ycb = cdiv(k, BTF_COLS);

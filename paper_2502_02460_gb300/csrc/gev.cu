@@ -59,7 +59,8 @@ size_t carve(Sys& s, char* base) {
   size_t oYk = L.add(n * n * es);
   size_t oZk = L.add(n * n * 8);
   size_t oprog = L.add(n * sizeof(int) + 64);
-  size_t panel = (size_t)4096 * (2 * b + 8) * es * 2;
+  // panel factorisation partial sums, double-buffered: 2 x 4096 norms, 2 x b pivot row, 2 x 4096 x b
+  size_t panel = (size_t)2 * 4096 * 8 + 2 * 128 * es + (size_t)2 * 4096 * b * es + 256;
   size_t opanel = L.add(panel);
   size_t ost = L.add(sizeof(int) * ST_COUNT);
   size_t ozb = 0;

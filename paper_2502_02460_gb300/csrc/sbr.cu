@@ -35,9 +35,17 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return t;  // valid in thread 0
 }
 
+// One grid barrier per column.  Before the barrier every block sums, over its rows below the pivot,
+// ||x||^2, u_j = sum_r conj(x_r) P(r, j) (j > c, the columns to update) and t_j = sum_r conj(P(r, j)) x_r
+// (j < c, the stored reflectors, for T), with the UNSCALED column x; the block holding the pivot row
+// publishes that row.  After the barrier each block forms the reflector (beta, tau, scale: v_c = 1,
+// v_r = scale x_r) and recovers the inner products exactly as
+//   w_j = v^H P(:, j) = P(c, j) + conj(scale) u_j,     s_j = Y(:, j)^H v = conj(P(c, j)) + scale t_j.
+// The partial-sum buffers alternate with the column's parity: a block may start column c + 1 while a
+// slower one still reads column c's sums, but column c + 2 waits for everyone at barrier c + 1.
 template <class T>
 __global__ void __launch_bounds__(NT) k_panel_qr(int m, int b, T* P, long long ldp, T* Y, long long ldy,
-                                                 T* Tm, double* nrm_part, T* w_part, T* alpha_g,
+                                                 T* Tm, double* nrm_part, T* w_part, T* prow,
                                                  GridBar gb, int R, int use_smem) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int blk = blockIdx.x, tid = threadIdx.x;
@@ -45,6 +53,7 @@ __global__ void __launch_bounds__(NT) k_panel_qr(int m, int b, T* P, long long l
   const int hi = min(m, lo + R);
   const int rows = max(0, hi - lo);
   const long long lds = R | 1;
+  const int G = gridDim.x;
   T* sm = reinterpret_cast<T*>(smraw);
   T* scratch = use_smem ? sm + lds * b : sm;
   T* red2 = scratch;          // NT entries
@@ -70,31 +79,49 @@ __global__ void __launch_bounds__(NT) k_panel_qr(int m, int b, T* P, long long l
       if (blk == 0 && tid < b) Tm[tid + c * b] = zero_<T>();
       continue;
     }
-    // ---- A: squared norm of the column below the pivot row
+    const int par = c & 1;
+    double* np_ = nrm_part + (size_t)par * G;
+    T* wp_ = w_part + (size_t)par * G * b;
+    T* pr_ = prow + (size_t)par * b;
+    // ---- A: partial sums over this block's rows strictly below the pivot, unscaled column x
+    const int r0 = max(0, c + 1 - lo);
     double ss = 0.0;
-    for (int r = max(0, c + 1 - lo) + tid; r < rows; r += NT) ss += abs2_(base[r + c * ld]);
-    double tot = block_sum<T>(ss, red);
-    if (tid == 0) {
-      nrm_part[blk] = tot;
-      if (lo <= c && c < hi) alpha_g[0] = base[(c - lo) + c * ld];
+    for (int r = r0 + tid; r < rows; r += NT) ss += abs2_(base[r + c * ld]);
+    const double tot = block_sum<T>(ss, red);
+    {
+      T acc = zero_<T>();
+      if (grp < NG && jj != c)
+        for (int r = r0 + grp; r < rows; r += NG) {
+          const T x = base[r + c * ld], pj = base[r + jj * ld];
+          acc += (jj > c) ? cmul(x, pj) : cmul(pj, x);
+        }
+      red2[tid] = acc;
+      __syncthreads();
+      if (tid < b) {
+        T sum = zero_<T>();
+        for (int g = 0; g < NG; ++g) sum += red2[g * b + tid];
+        wp_[(long long)blk * b + tid] = sum;
+      }
     }
+    if (tid == 0) np_[blk] = tot;
+    if (lo <= c && c < hi && tid < b) pr_[tid] = base[(c - lo) + tid * ld];  // the pivot row
     if (!grid_sync(gb, 101)) return;
-    // ---- B: reflector (all threads sum the block partials, in a fixed order)
+    // ---- B: the reflector (all blocks compute it from the same sums, in a fixed order)
     double xpart = 0.0;
-    for (int q = tid; q < (int)gridDim.x; q += NT) xpart += ldcg_(&nrm_part[q]);
+    for (int q = tid; q < G; q += NT) xpart += ldcg_(&np_[q]);
     const double xn_all = block_sum<T>(xpart, red);
     if (tid == 0) {
       const double xn = xn_all;
-      T alpha = ldcg_(alpha_g);
-      int trivial = (xn == 0.0 && im_(alpha) == 0.0);
+      const T alpha = ldcg_(&pr_[c]);
+      const int trivial = (xn == 0.0 && im_(alpha) == 0.0);
       if (trivial) {
         sh_tau = zero_<T>();
         sh_beta = alpha;
         sh_scale = zero_<T>();
       } else {
-        double nrm = sqrt(abs2_(alpha) + xn);
-        double beta = re_(alpha) >= 0.0 ? -nrm : nrm;
-        T bt = from_re<T>(beta);
+        const double nrm = sqrt(abs2_(alpha) + xn);
+        const double beta = re_(alpha) >= 0.0 ? -nrm : nrm;
+        const T bt = from_re<T>(beta);
         sh_tau = div_(bt - alpha, bt);
         sh_beta = bt;
         sh_scale = div_(from_re<T>(1.0), alpha - bt);
@@ -108,43 +135,25 @@ __global__ void __launch_bounds__(NT) k_panel_qr(int m, int b, T* P, long long l
       continue;  // uniform over the grid: every block computed the same reflector
     }
     const T scale = sh_scale;
-    for (int r = max(0, c + 1 - lo) + tid; r < rows; r += NT) base[r + c * ld] = scale * base[r + c * ld];
-    if (tid == 0 && lo <= c && c < hi) base[(c - lo) + c * ld] = sh_beta;
-    __syncthreads();
-    // ---- partial inner products: w_j = v^H P(:, j) (j > c), s_j = Y(:, j)^H v (j < c)
-    {
-      T acc = zero_<T>();
-      if (grp < NG && jj != c) {
-        for (int r = max(0, c - lo) + grp; r < rows; r += NG) {
-          const T vr = (lo + r == c) ? from_re<T>(1.0) : base[r + c * ld];
-          const T x = base[r + jj * ld];
-          acc += (jj > c) ? cmul(vr, x) : cmul(x, vr);
-        }
-      }
-      red2[tid] = acc;
-      __syncthreads();
-      if (tid < b) {
-        T sum = zero_<T>();
-        for (int g = 0; g < NG; ++g) sum += red2[g * b + tid];
-        w_part[(long long)blk * b + tid] = sum;
-      }
-    }
-    if (!grid_sync(gb, 102)) return;
-    // ---- C: apply H^H to the remaining columns; column c of T (block 0).  The block partials of
-    // w are summed by NG threads per column, then combined in a fixed order.
+    // the block partials of u / t, summed by NG threads per column, then in a fixed order
     {
       T part = zero_<T>();
       if (grp < NG)
-        for (int q = grp; q < (int)gridDim.x; q += NG) part += ldcg_(&w_part[(long long)q * b + jj]);
+        for (int q = grp; q < G; q += NG) part += ldcg_(&wp_[(long long)q * b + jj]);
       red2[tid] = part;
       __syncthreads();
       if (tid < b) {
         T sum = zero_<T>();
         for (int g = 0; g < NG; ++g) sum += red2[g * b + tid];
-        wv[tid] = sum;
+        const T pc = ldcg_(&pr_[tid]);
+        // w_j = P(c, j) + conj(scale) u_j (j > c);  s_j = conj(P(c, j)) + scale t_j (j < c)
+        wv[tid] = (tid > c) ? pc + conj_(scale) * sum : (tid < c ? conj_(pc) + scale * sum : zero_<T>());
       }
-      __syncthreads();
     }
+    for (int r = r0 + tid; r < rows; r += NT) base[r + c * ld] = scale * base[r + c * ld];
+    if (tid == 0 && lo <= c && c < hi) base[(c - lo) + c * ld] = sh_beta;
+    __syncthreads();
+    // ---- C: apply H^H to the remaining columns; column c of T (block 0)
     const T ctau = conj_(tau);
     if (grp < NG && jj > c) {
       const T wj = ctau * wv[jj];
@@ -211,9 +220,9 @@ template <class T> int he2hb(Sys& s, T* A, int lda, int b) {
   T* W1 = W0 + (size_t)n * 2 * s.b;
   T* sm0 = (T*)s.small;
   T* sm1 = sm0 + (size_t)s.b * s.b;
-  double* nrm_part = (double*)s.panelws;
-  T* alpha_g = (T*)(nrm_part + 4096);
-  T* w_part = alpha_g + 2;
+  double* nrm_part = (double*)s.panelws;     // 2 x 4096 (by column parity)
+  T* prow = (T*)(nrm_part + 2 * 4096);        // 2 x b pivot rows
+  T* w_part = prow + 2 * 128;                 // 2 x 4096 x b
   GridBar gb{(unsigned*)&s.status[ST_BARRIER_CNT], (unsigned*)&s.status[ST_BARRIER_GEN], s.status,
              &s.status[ST_ABORT]};
   const T one = from_re<T>(1.0), mone = from_re<T>(-1.0), zero = zero_<T>(), mhalf = from_re<T>(-0.5);
@@ -240,7 +249,7 @@ template <class T> int he2hb(Sys& s, T* A, int lda, int b) {
     GEV_CUDA_TRY(cudaMemsetAsync(&s.status[ST_BARRIER_CNT], 0, 2 * sizeof(int), s.stream));
     int mm = m, bb = b;
     long long ldp = lda, ldy = n;
-    void* args[] = {&mm, &bb, &Pp, &ldp, &Yp, &ldy, &Tp, &nrm_part, &w_part, &alpha_g, &gb, &R, &use_smem};
+    void* args[] = {&mm, &bb, &Pp, &ldp, &Yp, &ldy, &Tp, &nrm_part, &w_part, &prow, &gb, &R, &use_smem};
     GEV_COUNT(s);
     GEV_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_panel_qr<T>, dim3(G), dim3(NT), args, smem, s.stream));
     // ---- two-sided update of the trailing block, the rank-2b update as ONE product:
