@@ -245,6 +245,15 @@ def oracle_full_configs(threads_list=(None, 1), include_n4096=True):
             out.append({"n": n, "k": k, "seed": seed, "threads": nt if set_threads else None, "s": t,
                         "info": info, "max_abs_eig_err_vs_construction": float(np.max(np.abs(w - p.lam[:k]))),
                         "resid": dg["resid"], "ortho": dg["ortho"]})
+        try:  # context only: LAPACK through scipy on the same cores (neither the oracle nor the target)
+            import scipy.linalg as sla
+
+            t0 = time.perf_counter()
+            ws = sla.eigh(p.H, p.S, subset_by_index=[0, k - 1], eigvals_only=False)[0]
+            out.append({"n": n, "k": k, "context": "scipy.linalg.eigh (LAPACK)", "s": time.perf_counter() - t0,
+                        "max_abs_eig_err_vs_construction": float(np.max(np.abs(ws - p.lam[:k])))})
+        except ImportError:
+            pass
     if set_threads is not None:
         set_threads(cores)
     return out
