@@ -441,11 +441,42 @@ __global__ void __launch_bounds__(BTF_COLS) k_bt_level_f32(int n, int k, int L, 
 // and W_j = V T (2b x b, column-major at W + j 2b b) is written for the second product.  A reflector
 // with tau = 0 (a task that never ran) is a zero column.  One block of 256 threads per D_j: the Gram
 // entries V^H V by all threads (padded shared-memory columns), the recurrence by one warp, W by all.
+// The blocks of level L: groups g in [g_lo, g_lo + nblk) with task t = L - (ngroups - 1 - g) in
+// range and a window start w0(g) = (2g + L - ngroups + 1) b + 1 below n; w00 = w0(g_lo); windows are
+// 2b apart.  (Host and device.)
+struct LevelBlocks {
+  int g_lo, nblk, w00;
+};
+__host__ __device__ inline LevelBlocks level_blocks(int n, int b, int L, int ngroups, int ntask) {
+  LevelBlocks lb{0, 0, 0};
+  const int g_lo = max(0, ngroups - 1 - L);
+  int g_hi = min(ngroups - 1, ntask - 1 + ngroups - 1 - L);
+  while (g_hi >= g_lo && (2 * g_hi + L - ngroups + 1) * b + 1 >= n) --g_hi;
+  if (g_hi < g_lo) return lb;
+  lb.g_lo = g_lo;
+  lb.nblk = g_hi - g_lo + 1;
+  lb.w00 = (2 * g_lo + L - ngroups + 1) * b + 1;
+  return lb;
+}
+
+// Levels L0 .. L0 + nL - 1 in one grid: block x is block j of level L (levels in order), and its W
+// goes to W + (blocks of the earlier levels of the range + j) 2b b.
 template <class T>
-__global__ void __launch_bounds__(256) k_wy_level(int n, int b, int L, int ngroups, int g_lo, int w00, int ntask,
+__global__ void __launch_bounds__(256) k_wy_level(int n, int b, int L0, int nL, int ngroups, int ntask,
                                                   const T* V2, const T* tau2, T* W) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int j = blockIdx.x, tid = threadIdx.x;
+  const int tid = threadIdx.x;
+  int j = blockIdx.x, L = L0, before = 0;
+  LevelBlocks lb = level_blocks(n, b, L, ngroups, ntask);
+  while (j >= lb.nblk && L < L0 + nL - 1) {
+    j -= lb.nblk;
+    before += lb.nblk;
+    ++L;
+    lb = level_blocks(n, b, L, ngroups, ntask);
+  }
+  if (j >= lb.nblk) return;
+  const int g_lo = lb.g_lo, w00 = lb.w00;
+  W += (size_t)before * 2 * b * b;
   const int g = g_lo + j, t = L - (ngroups - 1 - g);
   const int m = 2 * b, ldv = m + 1;     // padded: column q of V starts q (2b + 1) elements in
   T* Vs = reinterpret_cast<T*>(smraw);  // 2b x b (ld 2b + 1)
@@ -565,23 +596,6 @@ template <class T> int hb2st(Sys& s, double* d, double* e) {
 
 template <class T, int COLS> int bt_levels(Sys& s, int n, int k, int b, T* Y, int ldy);
 
-// The blocks of level L: groups g in [g_lo, g_lo + nblk) with task t = L - (ngroups - 1 - g) in
-// range and a window start w0(g) = (g + t) b + 1 below n; w00 = w0(g_lo); windows are 2b apart.
-struct LevelBlocks {
-  int g_lo, nblk, w00;
-};
-inline LevelBlocks level_blocks(int n, int b, int L, int ngroups, int ntask) {
-  LevelBlocks lb{0, 0, 0};
-  const int g_lo = std::max(0, ngroups - 1 - L);
-  int g_hi = std::min(ngroups - 1, ntask - 1 + ngroups - 1 - L);
-  auto w0 = [&](int g) { return (2 * g + L - ngroups + 1) * b + 1; };
-  while (g_hi >= g_lo && w0(g_hi) >= n) --g_hi;
-  if (g_hi < g_lo) return lb;
-  lb.g_lo = g_lo;
-  lb.nblk = g_hi - g_lo + 1;
-  lb.w00 = w0(g_lo);
-  return lb;
-}
 
 // Y <- Q2 Y with every level applied as  P = blockdiag(V_j^H) Y_L,  Y_L -= blockdiag(V_j T_j) P  on the
 // emulated FP64 product engine (Y_L: the level's rows).  Returns GEV_ERR_UNSUPPORTED, before
@@ -592,7 +606,8 @@ template <class T> int bt_levels_wy(Sys& s, int n, int k, int b, T* Y, int ldy) 
   const int ngroups = (n - 3) / b + 1;
   const int nlevels = ngroups + s.ntask;
   T* P = (T*)s.W1;  // (nblk b) x k products V^H Y (W1 is free during the back-transform)
-  T* Wb = (T*)s.Q;  // the level's W_j blocks, nblk x 2b x b
+  T* Wb = (T*)s.Q;  // the W_j blocks of LCHUNK consecutive levels (Q is free once the divide and conquer is done)
+  constexpr int LCHUNK = 16;
   size_t need = 0;
   int max_nblk = 0;
   for (int L = 0; L < nlevels; ++L) {
@@ -609,21 +624,31 @@ template <class T> int bt_levels_wy(Sys& s, int n, int k, int b, T* Y, int ldy) 
     }
   }
   if (need > s.ozws_bytes || (size_t)max_nblk * b * k * sizeof(T) > (size_t)n * n * sizeof(T) ||
-      (size_t)max_nblk * 2 * b * b * sizeof(T) > (size_t)n * n * sizeof(double))
+      (size_t)LCHUNK * max_nblk * 2 * b * b * sizeof(T) > (size_t)n * n * sizeof(double))
     return GEV_ERR_UNSUPPORTED;
   const size_t smem = sizeof(T) * ((size_t)(2 * b + 1) * b + (size_t)b * (b + 1) + b) + 64;
   GEV_TRY(allow_dyn_smem(k_wy_level<T>, smem));
+  size_t woff = 0;  // offset of level L's blocks in Wb (elements)
   for (int L = 0; L < nlevels; ++L) {
+    if (L % LCHUNK == 0) {  // the compact-WY blocks of the next LCHUNK levels, in one grid
+      int nb = 0;
+      for (int l = L; l < std::min(nlevels, L + LCHUNK); ++l) nb += level_blocks(n, b, l, ngroups, s.ntask).nblk;
+      if (nb > 0) {
+        GEV_COUNT(s);
+        k_wy_level<T><<<nb, 256, smem, s.stream>>>(n, b, L, std::min(LCHUNK, nlevels - L), ngroups, s.ntask,
+                                                   (const T*)s.V2, (const T*)s.tau2, Wb);
+      }
+      woff = 0;
+    }
     const LevelBlocks lb = level_blocks(n, b, L, ngroups, s.ntask);
     if (lb.nblk == 0) continue;
     const int rows = std::min(lb.nblk * 2 * b, n - lb.w00);
-    GEV_COUNT(s);
-    k_wy_level<T><<<lb.nblk, 256, smem, s.stream>>>(n, b, L, ngroups, lb.g_lo, lb.w00, s.ntask, (const T*)s.V2,
-                                                    (const T*)s.tau2, Wb);
+    T* Wl = Wb + woff;
+    woff += (size_t)lb.nblk * 2 * b * b;
     BdOp a1{1, cx, b, n, s.ntask, lb.g_lo, L, ngroups, lb.nblk, lb.w00, s.V2, s.tau2, nullptr};
     T* Yl = Y + lb.w00;
     const int M1 = lb.nblk * b;
-    BdOp a2{2, cx, b, n, s.ntask, lb.g_lo, L, ngroups, lb.nblk, lb.w00, nullptr, nullptr, Wb};
+    BdOp a2{2, cx, b, n, s.ntask, lb.g_lo, L, ngroups, lb.nblk, lb.w00, nullptr, nullptr, Wl};
     if constexpr (f32) {
       if (!gemm_f32_bdiag(s, M1, k, rows, a1, b, 2 * b, Yl, ldy, 1.f, 0.f, P, M1)) return GEV_ERR_CUDA;
       if (!gemm_f32_bdiag(s, rows, k, M1, a2, 2 * b, b, P, M1, -1.f, 1.f, Yl, ldy)) return GEV_ERR_CUDA;

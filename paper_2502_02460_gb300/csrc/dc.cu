@@ -332,26 +332,42 @@ __global__ void __launch_bounds__(1024) k_merge_prep(int n, Node* nodes, const d
 }
 
 // --------------------------------------------------------------------------- merge: secular --
+// The secular function and its pieces at mu, by one warp: lane l sums the poles l, l + 32, ...; the
+// partial sums are reduced to lane 0 in a fixed order and broadcast, so every lane holds the same bits
+// (the root iteration below branches on them identically in all lanes).
 __device__ void eval_secular(int K, int j, int o, const double* delta, const double* z, double r,
                              double mu, double& f, double& psi, double& dpsi, double& phi,
                              double& dphi) {
+  const int lane = threadIdx.x & 31;
   const double dO = delta[o];
-  psi = dpsi = phi = dphi = 0.0;
-  for (int i = 0; i < K; ++i) {
+  double a = 0.0, b = 0.0, c = 0.0, e = 0.0;
+  for (int i = lane; i < K; i += 32) {
     const double di = (delta[i] - dO) - mu;
     const double zi = z[i];
     const double t = zi / di;
-    if (i <= j) { psi += zi * t; dpsi += t * t; }
-    else { phi += zi * t; dphi += t * t; }
+    if (i <= j) { a += zi * t; b += t * t; }
+    else { c += zi * t; e += t * t; }
   }
+  for (int off = 16; off > 0; off >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, off);
+    b += __shfl_down_sync(0xffffffffu, b, off);
+    c += __shfl_down_sync(0xffffffffu, c, off);
+    e += __shfl_down_sync(0xffffffffu, e, off);
+  }
+  psi = __shfl_sync(0xffffffffu, a, 0);
+  dpsi = __shfl_sync(0xffffffffu, b, 0);
+  phi = __shfl_sync(0xffffffffu, c, 0);
+  dphi = __shfl_sync(0xffffffffu, e, 0);
   f = 1.0 + r * (psi + phi);
 }
 
-__global__ void k_secular(Node* nodes, DcArrays A, int* status) {
+// One warp per root (blockDim 256: 8 roots per block); lane 0 writes the result.
+__global__ void __launch_bounds__(256) k_secular(Node* nodes, DcArrays A, int* status) {
   const Node nd = nodes[blockIdx.y];
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const bool lead = (threadIdx.x & 31) == 0;
   const int K = nd.K;
-  if (j >= K) return;
+  if (j >= K) return;  // uniform per warp
   const int a = nd.a;
   const double* delta = A.nd_d + a;
   const double* z = A.nd_z + a;
@@ -416,6 +432,7 @@ __global__ void k_secular(Node* nodes, DcArrays A, int* status) {
     if (fabs(mnew - mu) <= 2.0 * EPS * fabs(mnew)) { mu = mnew; conv = true; break; }
     mu = mnew;
   }
+  if (!lead) return;
   if (!conv) atomicCAS(&status[ST_NOCONV], 0, 302);
   A.mu[a + j] = mu;
   A.org[a + j] = o;
@@ -629,7 +646,7 @@ int stedc(Sys& s, const double* d, const double* e, int k, double* w, double* Z,
     }
     if (Kmax > 0) {
       GEV_COUNT(s);
-      k_secular<<<dim3(cdiv(Kmax, 128), nnodes), 128, 0, st>>>(A.nodes, A, s.status);
+      k_secular<<<dim3(cdiv(Kmax, 8), nnodes), 256, 0, st>>>(A.nodes, A, s.status);
       GEV_COUNT(s);
       k_zprime<<<dim3(cdiv(Kmax, 128), nnodes), 128, 0, st>>>(A.nodes, A);
     }
