@@ -16,60 +16,144 @@ namespace {
 constexpr int NBMAX = 64;
 constexpr int LDS = NBMAX + 1;
 
-// X <- L^{-1} for the jb x jb lower-triangular L in shared memory (both column-major, ld LDS).
+constexpr int SB = 16;  // sub-block of the blocked leaf factorisation and inverse
+
+template <class T> __device__ __forceinline__ T shfl_(T v, int src);
+template <> __device__ __forceinline__ double shfl_<double>(double v, int src) {
+  return __shfl_sync(0xffffffffu, v, src);
+}
+template <> __device__ __forceinline__ zd shfl_<zd>(zd v, int src) {
+  return make_zd(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+
+// X <- L^{-1} for the jb x jb lower-triangular L in shared memory (both column-major, ld LDS; X fully
+// overwritten, zero above the diagonal), blocked by SB:
+//   the diagonal blocks X_ii = L_ii^{-1}: one warp each, lane c forms column c by forward substitution;
+//   then by block diagonals d = 1, 2, ...: S = sum_{k=j}^{i-1} L_ik X_kj for every block (i, j = i - d),
+//   and X_ij = -X_ii S (block columns are independent; a diagonal needs the previous ones).
+// tmp: (NBMAX / SB - 1) SB^2 elements of shared scratch.  Called by all threads of the block.
 template <class T>
-__device__ void inv_lower_smem(int jb, const T* L, T* X) {
-  for (int c = threadIdx.x; c < jb; c += blockDim.x) {
-    for (int i = 0; i < jb; ++i) {
-      T v = zero_<T>();
-      if (i >= c) {
+__device__ void inv_lower_blocked(int jb, const T* L, T* X, T* tmp) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nsb = (jb + SB - 1) / SB;
+  for (int t = tid; t < NBMAX * LDS; t += blockDim.x) X[t] = zero_<T>();
+  __syncthreads();
+  if (warp < nsb) {
+    const int k0 = warp * SB, bs = min(SB, jb - k0), c = lane;
+    if (c < bs) {
+      for (int i = c; i < bs; ++i) {
         T acc = (i == c) ? from_re<T>(1.0) : zero_<T>();
-        for (int p = c; p < i; ++p) acc -= L[i + p * LDS] * X[p + c * LDS];
-        v = (1.0 / re_(L[i + i * LDS])) * acc;
+        for (int p = c; p < i; ++p) acc -= L[(k0 + i) + (k0 + p) * LDS] * X[(k0 + p) + (k0 + c) * LDS];
+        X[(k0 + i) + (k0 + c) * LDS] = (1.0 / re_(L[(k0 + i) + (k0 + i) * LDS])) * acc;
       }
-      X[i + c * LDS] = v;
     }
+  }
+  __syncthreads();
+  for (int d = 1; d < nsb; ++d) {
+    const int nblk = nsb - d;  // blocks (i, j) = (j + d, j), j < nblk
+    for (int t = tid; t < nblk * SB * SB; t += blockDim.x) {
+      const int bj = t / (SB * SB), e = t % (SB * SB), r = e % SB, c = e / SB;
+      const int bi = bj + d, i0 = bi * SB, j0 = bj * SB;
+      T acc = zero_<T>();
+      if (i0 + r < jb && j0 + c < jb)
+        for (int k = j0; k < i0; ++k) acc += L[(i0 + r) + k * LDS] * X[k + (j0 + c) * LDS];
+      tmp[t] = acc;
+    }
+    __syncthreads();
+    for (int t = tid; t < nblk * SB * SB; t += blockDim.x) {
+      const int bj = t / (SB * SB), e = t % (SB * SB), r = e % SB, c = e / SB;
+      const int bi = bj + d, i0 = bi * SB, j0 = bj * SB;
+      if (i0 + r < jb && j0 + c < jb) {
+        T acc = zero_<T>();
+        for (int q = 0; q <= r; ++q) acc += X[(i0 + r) + (i0 + q) * LDS] * tmp[bj * SB * SB + q + c * SB];
+        X[(i0 + r) + (j0 + c) * LDS] = -acc;
+      }
+    }
+    __syncthreads();
   }
 }
 
-// Factor the jb x jb diagonal block in place (lower) and write its inverse to Dinv.
+// Factor the jb x jb diagonal block in place (lower) and write its inverse to Dinv, blocked by SB:
+// for each SB-column sub-panel, one warp factors the SB x SB diagonal block in registers (lane i holds
+// row i; the pivot column travels by shuffles), all threads solve the rows below against it and update
+// the trailing block.  A non-positive pivot records its index (first one, atomicCAS) and stops.
 template <class T>
 __global__ void k_potrf_diag(int jb, T* A, long long lda, T* Dinv, long long ldd, int* status, int j0) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* L = reinterpret_cast<T*>(smraw);
   T* X = L + NBMAX * LDS;
+  T* tmp = X + NBMAX * LDS;
   __shared__ int fail;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) fail = 0;
   for (int t = tid; t < jb * jb; t += blockDim.x) {
     int i = t % jb, j = t / jb;
     L[i + j * LDS] = (i >= j) ? A[i + j * lda] : zero_<T>();
   }
   __syncthreads();
-  for (int p = 0; p < jb; ++p) {
-    if (tid == 0) {
-      double d = re_(L[p + p * LDS]);
-      if (!(d > 0.0)) {
-        fail = 1;
-        atomicCAS(&status[ST_NOT_SPD], 0, j0 + p + 1);
+  for (int kb = 0; kb < jb; kb += SB) {
+    const int bs = min(SB, jb - kb);
+    // (a) the diagonal block, by warp 0
+    if (warp == 0) {
+      T r[SB];
+      const int i = lane;
+#pragma unroll
+      for (int j = 0; j < SB; ++j) r[j] = (i < bs && j <= i) ? L[(kb + i) + (kb + j) * LDS] : zero_<T>();
+      int bad = -1;
+#pragma unroll
+      for (int p = 0; p < SB; ++p) {
+        if (p < bs && bad < 0) {  // uniform over the warp
+          const double dpp = re_(shfl_(r[p], p));
+          if (!(dpp > 0.0)) {
+            bad = p;
+          } else {
+            const double piv = sqrt(dpp);
+            if (i == p) r[p] = from_re<T>(piv);
+            else if (i > p) r[p] = (1.0 / piv) * r[p];
+#pragma unroll
+            for (int j = p + 1; j < SB; ++j) {
+              const T ljp = shfl_(r[p], j);
+              if (j < bs && i >= j && i < bs) r[j] -= mulc(r[p], ljp);
+            }
+          }
+        }
+      }
+      if (bad >= 0) {
+        if (lane == 0) {
+          fail = 1;
+          atomicCAS(&status[ST_NOT_SPD], 0, j0 + kb + bad + 1);
+        }
       } else {
-        L[p + p * LDS] = from_re<T>(sqrt(d));
+#pragma unroll
+        for (int j = 0; j < SB; ++j)
+          if (i < bs && j <= i) L[(kb + i) + (kb + j) * LDS] = r[j];
       }
     }
     __syncthreads();
     if (fail) return;
-    const double inv = 1.0 / re_(L[p + p * LDS]);
-    for (int i = p + 1 + tid; i < jb; i += blockDim.x) L[i + p * LDS] = inv * L[i + p * LDS];
+    const int r0 = kb + bs, nr = jb - r0;
+    if (nr <= 0) break;
+    // (b) rows below: L21 = A21 L11^{-H}, one thread per row
+    for (int i = r0 + tid; i < jb; i += blockDim.x) {
+      for (int p = 0; p < bs; ++p) {
+        T x = L[i + (kb + p) * LDS];
+        for (int q = 0; q < p; ++q) x -= mulc(L[i + (kb + q) * LDS], L[(kb + p) + (kb + q) * LDS]);
+        L[i + (kb + p) * LDS] = (1.0 / re_(L[(kb + p) + (kb + p) * LDS])) * x;
+      }
+    }
     __syncthreads();
-    const int r = jb - p - 1;
-    for (int t = tid; t < r * r; t += blockDim.x) {
-      int i = p + 1 + t % r, j = p + 1 + t / r;
-      if (j <= i) L[i + j * LDS] -= mulc(L[i + p * LDS], L[j + p * LDS]);
+    // (c) trailing update A22 -= L21 L21^H (lower triangle)
+    for (int t = tid; t < nr * nr; t += blockDim.x) {
+      const int i = r0 + t % nr, j = r0 + t / nr;
+      if (j <= i) {
+        T acc = zero_<T>();
+        for (int p = 0; p < bs; ++p) acc += mulc(L[i + (kb + p) * LDS], L[j + (kb + p) * LDS]);
+        L[i + j * LDS] -= acc;
+      }
     }
     __syncthreads();
   }
-  inv_lower_smem(jb, L, X);
-  __syncthreads();
+  inv_lower_blocked(jb, L, X, tmp);
   for (int t = tid; t < jb * jb; t += blockDim.x) {
     int i = t % jb, j = t / jb;
     A[i + j * lda] = (i >= j) ? L[i + j * LDS] : zero_<T>();
@@ -90,15 +174,14 @@ __global__ void k_inv_diag_blocks(int n, int nb, const T* A, long long lda, T* D
     L[i + j * LDS] = (i >= j) ? A[(j0 + i) + (long long)(j0 + j) * lda] : zero_<T>();
   }
   __syncthreads();
-  inv_lower_smem(jb, L, X);
-  __syncthreads();
+  inv_lower_blocked(jb, L, X, X + NBMAX * LDS);
   for (int t = threadIdx.x; t < jb * jb; t += blockDim.x) {
     int i = t % jb, j = t / jb;
     Dinv[i + (long long)(j0 + j) * nb] = X[i + j * LDS];
   }
 }
 
-template <class T> size_t diag_smem() { return sizeof(T) * 2 * NBMAX * LDS; }
+template <class T> size_t diag_smem() { return sizeof(T) * (2 * NBMAX * LDS + (NBMAX / SB - 1) * SB * SB); }
 
 template <class T> int set_smem_attrs() {
   GEV_TRY(allow_dyn_smem(k_potrf_diag<T>, diag_smem<T>()));
