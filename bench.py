@@ -503,6 +503,8 @@ def main():
     ap.add_argument("--fp32-products", type=int, default=-1, choices=[-1, 0, 3, 6],
                     help="mixed form, FP32 products: 6 / 3 = BF16x6 / BF16x3 on the tensor cores, "
                          "0 = FP32 CUDA cores, -1 = automatic")
+    ap.add_argument("--rr-band-b", type=int, default=0, choices=[0, 16, 32, 64],
+                    help="mixed form: band width of the refinement's Rayleigh-Ritz solve (0 = automatic)")
     ap.add_argument("--fp64-emulation", type=int, default=-1, choices=[-1, 0, 1],
                     help="FP64 products of the headline solve: 1 = BF16 digit planes on the tensor "
                          "cores, 0 = native DMMA, -1 = automatic (1)")
@@ -553,7 +555,7 @@ def main():
     stream = torch.cuda.current_stream(dev)
     solver = gev.Solver(args.n, complex_=args.complex, device=dev, mixed=args.mixed,
                         band_b=args.band_b, timing=2, stream=stream, fp64_emulation=args.fp64_emulation,
-                        fp32_products=args.fp32_products)
+                        fp32_products=args.fp32_products, rr_band_b=args.rr_band_b)
     w = torch.empty(args.k, dtype=torch.float64, device=dev)
     Cb = torch.empty((args.k, args.n), dtype=solver.dtype, device=dev)
     for _ in range(args.warmup):
@@ -642,7 +644,7 @@ def main():
             plain_emu = time_plain(1, args.plain_steps)
         solver = gev.Solver(args.n, complex_=args.complex, device=dev, mixed=args.mixed,
                             band_b=args.band_b, timing=0, stream=stream, fp64_emulation=args.fp64_emulation,
-                            fp32_products=args.fp32_products)
+                            fp32_products=args.fp32_products, rr_band_b=args.rr_band_b)
     # end-to-end through the Python API with pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -671,7 +673,7 @@ def main():
         solver.close()
         cs = gev.Solver(args.n, complex_=args.complex, device=dev, mixed=args.mixed, band_b=args.band_b,
                         stream=stream, fp64_emulation=args.fp64_emulation, fp32_products=args.fp32_products,
-                        check=True)
+                        check=True, rr_band_b=args.rr_band_b)
         cs.solve_cm(Hb, Sb, args.k, w, Cb)
         accuracy = {"resid": cs.last_report["resid"], "ortho": cs.last_report["ortho"],
                     "bound_resid": 1e-11 if args.mixed else 1e-13 * args.n ** 0.5,

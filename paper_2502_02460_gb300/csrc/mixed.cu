@@ -31,6 +31,13 @@ namespace gev {
 
 namespace {
 
+// band width of the k x k Rayleigh-Ritz solve: the caller's choice, else 32 (its FP64 bulge chasing, all k
+// pairs, sits on a 3k-task critical path whose task cost grows as b^2)
+int rr_band(int want, int k) {
+  if (want == 16 || want == 32 || want == 64) return want;
+  return k >= 64 ? 32 : 0;
+}
+
 __device__ __forceinline__ double wsum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   return v;
@@ -364,7 +371,7 @@ int solve_mixed(Sys& s, const double* H, int ldh, const double* S, int lds, int 
     o.prec = GEV_PLAIN;
     o.timing = 0;
     o.workspace_limit = 0;
-    o.band_b = 0;
+    o.band_b = rr_band(s.opts.rr_band_b, k);
     o.fp64_emulation = s.emu_fp64;  // the Ritz pencil's products use the same FP64 engine
     o.check = 0;
     o.debug_stall = 0;
@@ -588,7 +595,7 @@ int solve_mixed_cx(Sys& s, const zd* H, int ldh, const zd* S, int lds, int k, do
     o.prec = GEV_PLAIN;
     o.timing = 0;
     o.workspace_limit = 0;
-    o.band_b = 0;
+    o.band_b = rr_band(s.opts.rr_band_b, k);
     o.fp64_emulation = s.emu_fp64;
     o.check = 0;
     o.debug_stall = 0;

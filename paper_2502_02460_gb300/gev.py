@@ -50,7 +50,8 @@ class Opts(ctypes.Structure):
                 ("refine_max_iter", ctypes.c_int), ("workspace_limit", ctypes.c_size_t),
                 ("timing", ctypes.c_int), ("fp64_emulation", ctypes.c_int),
                 ("refine_rr_only", ctypes.c_int), ("fp32_products", ctypes.c_int),
-                ("wait_limit", ctypes.c_int), ("check", ctypes.c_int), ("debug_stall", ctypes.c_int)]
+                ("wait_limit", ctypes.c_int), ("check", ctypes.c_int), ("debug_stall", ctypes.c_int),
+                ("rr_band_b", ctypes.c_int)]
 
 
 class Report(ctypes.Structure):
@@ -151,7 +152,7 @@ class Solver:
                  band_b: int = 0, panel_nb: int = 0, timing: int = 0, stream=None,
                  workspace_limit: int = 0, refine_tol: float = 0.0, refine_max_iter: int = 0,
                  fp64_emulation: int = -1, refine_rr_only: int = 0, fp32_products: int = -1,
-                 wait_limit: int = 0, check: bool = False, debug_stall: bool = False):
+                 wait_limit: int = 0, check: bool = False, debug_stall: bool = False, rr_band_b: int = 0):
         import torch
 
         if not torch.cuda.is_available():
@@ -185,6 +186,7 @@ class Solver:
         o.wait_limit = int(wait_limit)
         o.check = 1 if check else 0
         o.debug_stall = 1 if debug_stall else 0
+        o.rr_band_b = int(rr_band_b)
         self.opts = o
         h = ctypes.c_void_p()
         _check(lib().gev_setup(ctypes.byref(h), n, GEV_C128 if complex_ else GEV_F64, ctypes.byref(o)),
