@@ -313,7 +313,8 @@ __device__ __forceinline__ double scale2(double x, int e) {
 }
 
 
-__global__ void __maxnreg__(200) ozaki_kernel(OzP p) {  // one CTA of NTH threads per SM (512 TMEM columns)
+// (a 10-warp CTA puts 3 warps on one SM sub-partition of 16K registers: at most 168 registers per thread)
+__global__ void __launch_bounds__(NTH, 1) ozaki_kernel(OzP p) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // grouped raster: GROUP_M row tiles sweep the column tiles together
@@ -519,20 +520,20 @@ __global__ void __maxnreg__(200) ozaki_kernel(OzP p) {  // one CTA of NTH thread
       }
       if (gi < p.M) {
 #pragma unroll
-        for (int h = 0; h < 16; h += 16) {
-          // the loads of 16 outputs (column exponents, C) first, so that they overlap
+        for (int h = 0; h < 16; h += 8) {
+          // the loads of 8 outputs (column exponents, C) first, so that they overlap
           const bool read_c = p.ksplit == 1 && p.beta != 0.0;
-          double cin[16];
-          int fj[16];
+          double cin[8];
+          int fj[8];
 #pragma unroll
-          for (int u = 0; u < 16; ++u) {
+          for (int u = 0; u < 8; ++u) {
             const int gj = n0 + col0 + cb + h + u;
             const bool ok = gj < p.N && !(p.c_lower && (gi >> rs) < gj);
             fj[u] = (ok && any) ? p.F[gj] : EXP_ZERO;
             cin[u] = (ok && read_c) ? p.C[gi + gj * p.ldc] : 0.0;
           }
 #pragma unroll
-          for (int u = 0; u < 16; ++u) {
+          for (int u = 0; u < 8; ++u) {
             const int q = h + u;
             const int gj = n0 + col0 + cb + q;
             if (gj >= p.N || (p.c_lower && (gi >> rs) < gj)) continue;
