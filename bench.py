@@ -322,7 +322,7 @@ def run_stream(args, dev, mixed=False):
         H = p.H + (spec.dh_rel * np.linalg.norm(p.H) / np.linalg.norm(dH) * dH if it > 0 else 0)
         cache[(sid, it)] = gev.cm_from_numpy(H, dev)
     torch.cuda.synchronize()
-    srv = serve.Server(budget_bytes=120e9, workers=6, device=dev, mixed=mixed)
+    srv = serve.Server(budget_bytes=120e9, workers=args.stream_workers, device=dev, mixed=mixed)
     t0 = time.perf_counter()
     futs = []
     for (t, sid, it, n, k, last) in plan:
@@ -337,6 +337,7 @@ def run_stream(args, dev, mixed=False):
     st = srv.stats()
     st.update({"precision": "mixed (FP32 band reduction + FP64 refinement)" if mixed else "plain FP64",
                "dtype": "c128",
+               "workers": args.stream_workers,
                "workload": f"first {spec.requests} requests of the k-point stream (Poisson 200/s, "
                            f"N log-uniform in [{spec.n_min}, {spec.n_max}], 10 SCF iterations per "
                            f"system, S fixed, k = N/4)"})
@@ -491,6 +492,9 @@ def main():
     ap.add_argument("--stream-requests", type=int, default=32,
                     help="requests of the k-point serving stream reported beside (0 = none)")
     ap.add_argument("--stream-n-max", type=int, default=2048)
+    ap.add_argument("--stream-workers", type=int, default=12,
+                    help="concurrent solves of the serving stream (each on its own handle and stream; the "
+                         "device-memory budget of 120 GB bounds the large ones)")
     ap.add_argument("--stream-full", action="store_true",
                     help="the whole k-point stream: 512 requests, N log-uniform in [256, 8192]")
     ap.add_argument("--configs", action="store_true",
