@@ -101,7 +101,7 @@ typedef struct {
   int debug_stall;       /* failure-path tests only: 1 = the bulge chasing waits on a flag that nothing
                             sets, so its bounded wait expires (GEV_ERR_TIMEOUT); 0 = off */
   int rr_band_b;         /* mixed form: band width of the FP64 Rayleigh-Ritz solve of the refinement
-                            (16, 32 or 64; 0 = automatic) */
+                            (16, 32 or 64; 0 = automatic: 64) */
 } gev_opts;
 
 typedef struct {

@@ -24,8 +24,7 @@
 // asynchronous copies into a 4-stage shared-memory ring.  Warp roles: warp 8 issues the copies,
 // warp 9 issues the 36 MMAs per slice (tcgen05, accumulators in TMEM: 6 exact diagonals + 1
 // shared, 64 columns each), warps 0-7 (one TMEM lane per output row, half of its 64 columns
-// each) drain the exact accumulators at every chunk end (while the next chunk's products start in the
-// slots already drained) and write C.  Every mbarrier wait is bounded; on expiry the kernel records
+// each) drain the exact accumulators at every chunk end and write C.  Every mbarrier wait is bounded; on expiry the kernel records
 // ST_TIMEOUT, waits (bounded) for its copies and MMAs in flight, frees TMEM and returns.
 #include <cuda_bf16.h>
 
@@ -54,13 +53,7 @@ constexpr int NEPI_W = 8;                  // epilogue warps: TMEM lanes 32 (w %
 constexpr int HC = ON / 2;                  // output columns per epilogue thread
 constexpr int NTH = 32 * (NEPI_W + 2);      // + copy warp 8 + MMA warp 9
 constexpr int TMEM_COLS_OZ = 512;
-// Tensor memory: seven rotating slots for the six exact diagonals d = 2..7 and one shared slot for
-// d = 8, 9 (8 x 64 columns).  In chunk c diagonal d uses slot (d - 2 - c) mod 7, so the chunk's first
-// diagonal lands in the slot the previous chunk left free and diagonal d waits only for the drain of
-// the previous chunk's diagonal d - 1: the next chunk's products overlap the drain.
-constexpr int NXSLOT = DEXACT;             // 7 rotating exact slots
-constexpr int SHARED_SLOT = NXSLOT;        // TMEM slot of d = 8, 9
-__device__ __forceinline__ int xslot(int d, int c) { return ((d - 2 - c) % NXSLOT + NXSLOT) % NXSLOT; }
+constexpr int SHARED_SLOT = DEXACT - 1;    // TMEM slot of d = 8, 9; exact d at slot d - 2
 constexpr int GROUP_M = 16;                // raster: 16 row tiles share their B slices in L2
 constexpr int EXP_BAD = 1 << 20;           // exponent marking a non-finite entry
 constexpr int EXP_ZERO = -4000;            // exponent of an all-zero vector
@@ -361,8 +354,8 @@ __global__ void __launch_bounds__(NTH, 1) ozaki_kernel(OzP p) {
   uint64_t* full = reinterpret_cast<uint64_t*>(ctrl);  // [NSTAGE]: slice landed
   uint64_t* empty = full + NSTAGE;                      // [NSTAGE]: slice consumed by the MMAs
   uint64_t* cfull = empty + NSTAGE;                     // chunk accumulated
-  uint64_t* sfree = cfull + 1;                          // [NXSLOT]: exact slot drained by the epilogue warps
-  uint64_t* done = sfree + NXSLOT;                      // all MMAs complete
+  uint64_t* cempty = cfull + 1;                         // chunk drained by the epilogue warps
+  uint64_t* done = cempty + 1;                          // all MMAs complete
   uint32_t* tslot = reinterpret_cast<uint32_t*>(ctrl + 256);
   volatile int* err = reinterpret_cast<volatile int*>(ctrl + 320);
   int* issued = reinterpret_cast<int*>(ctrl + 384);
@@ -373,8 +366,7 @@ __global__ void __launch_bounds__(NTH, 1) ozaki_kernel(OzP p) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(su32(&empty[s])));
     }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(su32(cfull)));
-    for (int x = 0; x < NXSLOT; ++x)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(su32(&sfree[x])), "r"(NEPI_W));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(su32(cempty)), "r"(NEPI_W));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(su32(done)));
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     *err = 0;
@@ -422,13 +414,13 @@ __global__ void __launch_bounds__(NTH, 1) ozaki_kernel(OzP p) {
     // ---- MMA warp: 36 digit-pair products per 16-deep slice
     if (lane == 0) {
       const uint32_t id = idesc_bf16(OM, ON);
-      int uses[NXSLOT];  // chunks that have written each exact slot so far
-#pragma unroll
-      for (int x = 0; x < NXSLOT; ++x) uses[x] = 0;
-      bool ok = true;
-      for (int s = 0; s < nst && ok; ++s) {
+      for (int s = 0; s < nst; ++s) {
         const int slot = s % NSTAGE, c = s / CHUNK;
         const bool chunk_start = (s % CHUNK) == 0;
+        if (chunk_start && c > 0 && !bar_wait(su32(cempty), (c - 1) & 1, err)) {
+          if (!*err) *err = 412;
+          break;
+        }
         if (!bar_wait(su32(&full[slot]), (s / NSTAGE) & 1, err)) {
           if (!*err) *err = 413;
           break;
@@ -443,28 +435,15 @@ __global__ void __launch_bounds__(NTH, 1) ozaki_kernel(OzP p) {
             const int d = pa + qb;
             int col, en;
             if (d <= DEXACT) {  // the first pair of diagonal d (pa = 1) restarts it at a chunk start
-              const int x = xslot(d, c);
-              col = x * ON;
+              col = (d - 2) * ON;
               en = (chunk_start && pa == 1) ? 0 : 1;
-              if (!en) {
-                // the slot's previous chunk must be drained before it is overwritten
-                if (uses[x] > 0 && !bar_wait(su32(&sfree[x]), (uses[x] - 1) & 1, err)) {
-                  if (!*err) *err = 412;
-                  ok = false;
-                  break;
-                }
-                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                ++uses[x];
-              }
             } else {  // the shared slot starts with the first MMA of d = 8 (pa = 1, qb = 7)
               col = SHARED_SLOT * ON;
               en = (s == 0 && pa == 1 && qb == DEXACT) ? 0 : 1;
             }
             mma_bf16(tmem + col, sdesc16(a0 + (pa - 1) * A_TILE), sdesc16(b0 + (qb - 1) * B_TILE), id, en);
           }
-          if (!ok) break;
         }
-        if (!ok) break;
         commit(su32(&empty[slot]));
         if ((s % CHUNK) == CHUNK - 1 || s == nst - 1) commit(su32(cfull));
       }
@@ -489,21 +468,19 @@ __global__ void __launch_bounds__(NTH, 1) ozaki_kernel(OzP p) {
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 #pragma unroll
       for (int d = 2; d <= DEXACT; ++d) {
-        const int x = xslot(d, c);
         uint32_t r0[16], r1[16];
-        tmem_ld16(lane_base + (uint32_t)(x * ON), r0);
-        tmem_ld16(lane_base + (uint32_t)(x * ON + 16), r1);
+        tmem_ld16(lane_base + (uint32_t)((d - 2) * ON), r0);
+        tmem_ld16(lane_base + (uint32_t)((d - 2) * ON + 16), r1);
         asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-        // this warp's part of slot x is read: the next chunk may overwrite it
-        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-        __syncwarp();
-        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(su32(&sfree[x])) : "memory");
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
           acc[q] += units49(r0[q]);
           acc[16 + q] += units49(r1[q]);
         }
       }
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(su32(cempty)) : "memory");
     }
     const bool any = good && nchunk > 0;
     const int gi = m0 + row;
