@@ -37,6 +37,11 @@ METRIC = "N=16384 gen. eigensolve s (FP64 vs mixed, resid≤1e-11); k-pt stream 
 FP64_NOMINAL_TF = 1.25      # GB300 FP64 (DMMA) nominal, dense
 BF16_NOMINAL_TF = 2250.0    # GB300 BF16 nominal, dense
 EMU_PAIRS = 36              # BF16 digit-pair products per emulated FP64 product (p + q <= 9, 8 planes)
+# DRAM bytes of one ozaki_kernel launch, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum,
+# --clock-control none) of the 4096^3 product, the order of the solve's largest products; the timed
+# products of a solve differ in shape, so the figure is that launch's, not a per-solve average
+OZAKI_TRAFFIC = {"bytes": 2.579e9 + 0.132e9,
+                 "case": "ozaki_kernel, one 4096x4096x4096 FP64 product (profiles/ozaki_kernel_gemm_f64_4096.md)"}
 FP64_FMA_TF = 1.00          # GB300 FP64 FMA pipe of the CUDA cores, measured (probe kernel)
 FP32_FMA_TF = 73.9          # GB300 FP32 FMA pipe of the CUDA cores, measured (probe kernel)
 
@@ -716,7 +721,8 @@ def main():
         "accuracy": accuracy,
         "roofline": {"bound": "tensor", "kernel": roof_kernel,
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "frac": (achieved / peak) if achieved else None, "traffic": OZAKI_TRAFFIC["bytes"],
+                     "traffic_case": OZAKI_TRAFFIC["case"],
                      "launches_timed": gemm_calls, "fp64_equivalent_tflops": fp64_tf,
                      "peak_source": peak_source},
         "cpu_baseline": cb, "e2e": e2e, "gpu_launches": launches * args.steps, "clocks": clk,

@@ -102,6 +102,12 @@ typedef struct {
                             sets, so its bounded wait expires (GEV_ERR_TIMEOUT); 0 = off */
   int rr_band_b;         /* mixed form: band width of the FP64 Rayleigh-Ritz solve of the refinement
                             (16, 32 or 64; 0 = automatic: 64) */
+  int one_stage;         /* 1: one-stage Householder tridiagonalisation (the ELPA1 form of the section
+                            "Usability and Tutorials", reported there as the faster GPU choice when all
+                            or most eigenpairs are wanted) with a single back-transform, instead of
+                            full -> band, bulge chasing and two back-transforms; plain form only
+                            (GEV_MIXED returns GEV_ERR_UNSUPPORTED).  Panel width = the band width
+                            option (16, 32 or 64).  0 = two-stage (default) */
 } gev_opts;
 
 typedef struct {

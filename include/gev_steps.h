@@ -44,6 +44,12 @@ int gev_step_he2hb(gev_sys* s, void* A, int lda, int b, int* b_used);
    reflectors of Q2 (and, for complex data, the diagonal phase matrix) stay in the handle. */
 int gev_step_hb2st(gev_sys* s, double* d, double* e);
 
+/* Step 4 in one stage (the ELPA1 form, section "Usability and Tutorials"): A (Hermitian, lower
+   triangle read, overwritten) = Q T Q^H with T real symmetric tridiagonal, Q = H_0 ... H_{n-2}
+   Householder reflectors kept in the handle for gev_step_back.  d (n) and e (n-1) are device
+   doubles receiving T.  Panel width = the handle's band width. */
+int gev_step_he2td(gev_sys* s, void* A, int lda, double* d, double* e);
+
 /* Step 5 (Solve): divide and conquer on the real symmetric tridiagonal (d, e) (device, n and
    n-1 doubles, not modified).  w (device, n) receives all eigenvalues ascending; Z (device, real
    n x k, ldz >= n) the eigenvectors of the k lowest.  *deflated (host, optional) = number of
@@ -52,7 +58,8 @@ int gev_step_stedc(gev_sys* s, const double* d, const double* e, int k, double* 
                    int ldz, int* deflated);
 
 /* Step 6 (Back): Y = Q1 Q2 Z for real Z (n x k, device) using the reflectors kept by steps 4a and
-   4b on this handle; Y has the handle's dtype. */
+   4b on this handle (or Y = Q Z after the one-stage step 4, whichever ran last); Y has the handle's
+   dtype. */
 int gev_step_back(gev_sys* s, const double* Z, int ldz, int k, void* Y, int ldy);
 
 /* Step 7 (Mult.): C = X^H Y, X lower triangular (n x n), Y n x k. */

@@ -257,14 +257,19 @@ struct Sys {
   double* d = nullptr;    // tridiagonal diagonal (n)
   double* e = nullptr;    // off-diagonal (n)
   double* w = nullptr;    // eigenvalues (n)
-  double* Q = nullptr;    // n x n divide-and-conquer eigenvectors
+  double* Q = nullptr;    // n x n divide-and-conquer eigenvectors (one-stage reduction: symv partial sums)
+  size_t q_bytes = 0;
   double* Q2 = nullptr;   // n x n divide-and-conquer scratch
   void* dcws = nullptr;   // divide-and-conquer per-level workspace
   size_t dcws_bytes = 0;
   void* Yk = nullptr;     // n x n back-transformed vectors (element size es)
   double* Zk = nullptr;   // n x n eigenvectors of the tridiagonal (divide-and-conquer output)
   int* prog = nullptr;    // n per-sweep progress counters of the bulge chasing
-  int nsbr_panels = 0;    // panels of the last full -> band reduction
+  int nsbr_panels = 0;    // panels of the last full -> band (or one-stage) reduction
+  int q1_pw = 0;          // their width (reflectors per panel)
+  int q1_off = 0;         // first row of panel p's block: p * q1_pw + q1_off (b, or 1 for one stage)
+  int q1_nrefl = 0;       // reflectors in all (the last panel may be narrower)
+  bool one_stage_used = false;  // the last reduction was the one-stage one (no band, no Q2)
   int dc_lowp = 0;        // 1: divide-and-conquer merge products in FP32 (mixed form)
   double* R1 = nullptr;   // mixed form: n x n FP64 refinement buffers (R1..R3)
   double* R2 = nullptr;
@@ -359,6 +364,9 @@ template <class T> int hb2st(Sys& s, double* d, double* e);
 int stedc(Sys& s, const double* d, const double* e, int k, double* w, double* Z, int ldz, int* deflated);
 template <class T> int back(Sys& s, const double* Z, int ldz, int k, T* Y, int ldy);
 template <class T> int bt_he2hb(Sys& s, T* Y, int ldy, int k);
+// one-stage Householder tridiagonalisation into s.d / s.e, and Y = Q Z for it (td1.cu)
+template <class T> int he2td(Sys& s, T* A, int lda);
+template <class T> int back_td(Sys& s, const double* Z, int ldz, int k, T* Y, int ldy);
 template <class T> int bt_hb2st(Sys& s, const double* Z, int ldz, int k, T* Y, int ldy);
 // P (and PE when non-null) = sum_l g_l conj(C_il) C_jl, g = occ (and occ * evals), both triangles
 template <class T>

@@ -43,7 +43,7 @@ size_t carve(Sys& s, char* base) {
   const size_t n = (size_t)s.n, es = s.es(), b = (size_t)s.b, nb = (size_t)s.nb;
   Layout L;
   size_t oA = L.add(n * n * es), oX = L.add(n * n * es), oW1 = L.add(n * n * es),
-         oV1 = L.add(n * n * es), oT1 = L.add(b * n * es), odinv = L.add(nb * (n + nb) * es),
+         oV1 = L.add(n * n * es), oT1 = L.add(b * (n + b) * es), odinv = L.add(nb * (n + nb) * es),
          oPn = L.add(4 * n * 2 * b * es), osmall = L.add(4 * b * b * es);
   size_t split = 4 * n * 2 * b * es;
   if (split < ((size_t)16 << 20)) split = (size_t)16 << 20;
@@ -53,7 +53,9 @@ size_t carve(Sys& s, char* base) {
   size_t oband = L.add((size_t)ldband * (n + 2 * b) * es);
   size_t oV2 = L.add(b * n * ntask * es), otau2 = L.add(n * ntask * es), ophase = L.add(n * 16);
   size_t od = L.add(n * 8), oe = L.add(n * 8), ow = L.add(n * 8);
-  size_t oQ = L.add(n * n * 8), oQ2 = L.add(n * n * 8);
+  const size_t ntl = (n + 63) / 64;
+  const size_t qbytes = std::max(n * n * 8, ntl * ntl * 64 * es);
+  size_t oQ = L.add(qbytes), oQ2 = L.add(n * n * 8);
   size_t dcws = 64 * n * 8 + ((size_t)1 << 20);
   size_t odc = L.add(dcws);
   size_t oYk = L.add(n * n * es);
@@ -86,7 +88,7 @@ size_t carve(Sys& s, char* base) {
     s.band = base + oband; s.ldband = ldband;
     s.V2 = base + oV2; s.tau2 = base + otau2; s.ntask = (int)ntask; s.phase = base + ophase;
     s.d = (double*)(base + od); s.e = (double*)(base + oe); s.w = (double*)(base + ow);
-    s.Q = (double*)(base + oQ); s.Q2 = (double*)(base + oQ2);
+    s.Q = (double*)(base + oQ); s.q_bytes = qbytes; s.Q2 = (double*)(base + oQ2);
     s.dcws = base + odc; s.dcws_bytes = dcws;
     s.Yk = base + oYk;
     s.Zk = (double*)(base + oZk);
@@ -260,6 +262,7 @@ int gev_solve(gev_sys* h, const void* H, int ldh, const void* S, int lds, int k,
   if (!S && !(s.reuse && s.have_factor && s.factor_kind == 0)) return GEV_ERR_REUSE_WITHOUT_FACTOR;
   if (cudaSetDevice(s.opts.device) != cudaSuccess) return GEV_ERR_CUDA;
   if (rep) std::memset(rep, 0, sizeof(*rep));
+  if (s.opts.one_stage && s.opts.prec == GEV_MIXED) return GEV_ERR_UNSUPPORTED;
   int r;
   if (s.opts.prec == GEV_MIXED && s.dtype == GEV_C128)
     r = solve_mixed_cx(s, (const zd*)H, ldh, (const zd*)S, lds, k, evals, (zd*)C, ldc, rep);
@@ -430,6 +433,24 @@ int gev_step_he2hb(gev_sys* h, void* A, int lda, int b, int* b_used) {
   return 0;
 }
 
+int gev_step_he2td(gev_sys* h, void* A, int lda, double* d, double* e) {
+  STEP_PROLOGUE(h)
+  if (!A) return -2;
+  if (lda < s.n) return -3;
+  if (!d) return -4;
+  if (!e && s.n > 1) return -5;
+  GEV_TRY(reset_status(s));
+  int r = s.dtype == GEV_C128 ? he2td<zd>(s, (zd*)A, lda) : he2td<double>(s, (double*)A, lda);
+  if (r) return r;
+  GEV_TRY(sync_status(s));
+  if (s.status_h[ST_TIMEOUT]) return GEV_ERR_TIMEOUT;
+  GEV_CUDA_TRY(cudaMemcpyAsync(d, s.d, sizeof(double) * s.n, cudaMemcpyDeviceToDevice, s.stream));
+  if (s.n > 1)
+    GEV_CUDA_TRY(cudaMemcpyAsync(e, s.e, sizeof(double) * (s.n - 1), cudaMemcpyDeviceToDevice, s.stream));
+  GEV_CUDA_TRY(cudaStreamSynchronize(s.stream));
+  return 0;
+}
+
 int gev_step_hb2st(gev_sys* h, double* d, double* e) {
   STEP_PROLOGUE(h)
   if (!d) return -2;
@@ -468,7 +489,7 @@ int gev_step_back(gev_sys* h, const double* Z, int ldz, int k, void* Y, int ldy)
   if (k < 1 || k > s.n) return -4;
   if (!Y) return -5;
   if (ldy < s.n) return -6;
-  if (!s.have_band || !s.have_tridiag_refl) return GEV_ERR_UNSUPPORTED;
+  if (!s.one_stage_used && (!s.have_band || !s.have_tridiag_refl)) return GEV_ERR_UNSUPPORTED;
   s.z_unit = false;  // the caller's Z: no bound on its entries is assumed
   int r = s.dtype == GEV_C128 ? back<zd>(s, Z, ldz, k, (zd*)Y, ldy) : back<double>(s, Z, ldz, k, (double*)Y, ldy);
   if (r) return r;
@@ -531,23 +552,26 @@ template <class T> int solve_t(Sys& s, const T* H, int ldh, const T* S, int lds,
   GEV_TRY(hegst<T>(s, H, ldh, X, n, A, n));
   s.have_factor = true;
   s.factor_kind = 0;
-  // steps 4a / 4b: two-stage tridiagonalisation
+  const bool one = s.opts.one_stage != 0;
+  // steps 4a / 4b: two-stage tridiagonalisation (or the one-stage reduction, timed as "to_tridiag")
   mark(GEV_STEP_TO_BAND);
-  GEV_TRY(he2hb<T>(s, A, n, s.b));
+  if (!one) GEV_TRY(he2hb<T>(s, A, n, s.b));
   mark(GEV_STEP_TO_TRIDIAG);
-  GEV_TRY(hb2st<T>(s, s.d, s.e));
+  if (one) GEV_TRY(he2td<T>(s, A, n));
+  else GEV_TRY(hb2st<T>(s, s.d, s.e));
   GEV_TRY(stop_on_timeout(s));
   // step 5: divide and conquer, k lowest vectors
   mark(GEV_STEP_SOLVE);
   GEV_TRY(stedc(s, s.d, s.e, k, s.w, s.Zk, n, nullptr));
-  // step 6: Y = Q1 Q2 Z
+  // step 6: Y = Q1 Q2 Z (one stage: Y = Q Z, timed as "back_tridiag")
   mark(GEV_STEP_BACK_TRIDIAG);
   T* Y = (T*)s.Yk;
   s.z_unit = true;  // the divide-and-conquer eigenvectors
-  GEV_TRY(bt_hb2st<T>(s, s.Zk, n, k, Y, n));
+  if (one) GEV_TRY(back_td<T>(s, s.Zk, n, k, Y, n));
+  else GEV_TRY(bt_hb2st<T>(s, s.Zk, n, k, Y, n));
   s.z_unit = false;
   mark(GEV_STEP_BACK_BAND);
-  GEV_TRY(bt_he2hb<T>(s, Y, n, k));
+  if (!one) GEV_TRY(bt_he2hb<T>(s, Y, n, k));
   // step 7: C = X^H Y
   mark(GEV_STEP_MULT);
   GEV_TRY(mult<T>(s, X, n, Y, n, k, C, ldc));

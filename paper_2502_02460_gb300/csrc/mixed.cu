@@ -375,6 +375,7 @@ int solve_mixed(Sys& s, const double* H, int ldh, const double* S, int lds, int 
     o.band_b = rr_band(s.opts.rr_band_b, k);
     o.fp64_emulation = s.emu_fp64;  // the Ritz pencil's products use the same FP64 engine
     o.check = 0;
+    o.one_stage = 0;
     o.debug_stall = 0;
     gev_sys* h = nullptr;
     const int rc = gev_setup(&h, k, GEV_F64, &o);
@@ -599,6 +600,7 @@ int solve_mixed_cx(Sys& s, const zd* H, int ldh, const zd* S, int lds, int k, do
     o.band_b = rr_band(s.opts.rr_band_b, k);
     o.fp64_emulation = s.emu_fp64;
     o.check = 0;
+    o.one_stage = 0;
     o.debug_stall = 0;
     gev_sys* h = nullptr;
     const int rc = gev_setup(&h, k, GEV_C128, &o);

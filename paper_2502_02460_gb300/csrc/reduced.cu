@@ -51,8 +51,12 @@ int solve_reduced(Sys& s, const T* H, int ldh, const T* S, int lds, double delta
     // 1. all eigenpairs of S
     GEV_TRY(copy_lower<T>(s, n, S, lds, A, n));
     GEV_TRY(mirror_lower<T>(s, n, A, n));
-    GEV_TRY(he2hb<T>(s, A, n, s.b));
-    GEV_TRY(hb2st<T>(s, s.d, s.e));
+    if (s.opts.one_stage) {
+      GEV_TRY(he2td<T>(s, A, n));
+    } else {
+      GEV_TRY(he2hb<T>(s, A, n, s.b));
+      GEV_TRY(hb2st<T>(s, s.d, s.e));
+    }
     GEV_TRY(stop_on_timeout(s));
     GEV_TRY(stedc(s, s.d, s.e, n, s.w, s.Zk, n, nullptr));
     T* D = (T*)s.Yk;
@@ -123,8 +127,12 @@ int solve_reduced(Sys& s, const T* H, int ldh, const T* S, int lds, double delta
   GEV_TRY(reset_status(u));
   T* Au = (T*)u.A;
   GEV_TRY(copy2d<T>(u, m, m, A, m, Au, m));
-  GEV_TRY(he2hb<T>(u, Au, m, u.b));
-  GEV_TRY(hb2st<T>(u, u.d, u.e));
+  if (u.opts.one_stage) {
+    GEV_TRY(he2td<T>(u, Au, m));
+  } else {
+    GEV_TRY(he2hb<T>(u, Au, m, u.b));
+    GEV_TRY(hb2st<T>(u, u.d, u.e));
+  }
   GEV_TRY(stop_on_timeout(u));
   GEV_TRY(stedc(u, u.d, u.e, k, u.w, u.Zk, m, nullptr));
   T* Yu = (T*)u.Yk;

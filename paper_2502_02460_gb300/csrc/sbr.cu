@@ -290,50 +290,61 @@ template <class T> int he2hb(Sys& s, T* A, int lda, int b) {
   s.have_band = true;
   s.have_tridiag_refl = false;
   s.nsbr_panels = npanel;
+  s.q1_pw = b;
+  s.q1_off = b;
+  s.q1_nrefl = npanel * b;
+  s.one_stage_used = false;
   return 0;
 }
 
 // Y <- Q1 Y (n x k), Q1 = Q_0 Q_1 ... Q_last: the panels' compact-WY blocks, applied G panels at a
-// time.  Consecutive panels p .. p+G-1 merge into one block  Q_p ... Q_{p+G-1} = I - Yg Tg Yg^H  with
-// Yg = [Y_p ... Y_{p+G-1}] (the stored columns of V1 from row r0_p on: each Y_j is zero above its own
-// first row, V1 being cleared before the reduction) and Tg upper triangular, built block column by
-// block column from the panels' T_j and the Gram blocks Yg^H Yg:
-//     Tg(0:jb, jb:(j+1)b) = -Tg(0:jb, 0:jb) (Yg(:, 0:jb)^H Y_j) T_j,   Tg(jb.., jb..) = T_j.
-// Each group then costs three products with inner dimension G b (or m), applied last group first.
+// time.  Panel p holds reflectors p*pw .. p*pw + w_p - 1 (w_p = pw but for a narrower last panel of
+// the one-stage reduction), stored in those columns of V1 from row p*pw + off on (off = b for the
+// full -> band panels, 1 for the one-stage ones), each zero above its own first row (V1 is cleared
+// before the reduction), with its w_p x w_p factor T_p at T1 + p pw^2 (ld pw).  Consecutive panels
+// p .. p+G-1 merge into one block  Q_p ... Q_{p+G-1} = I - Yg Tg Yg^H,  Yg = [Y_p ... Y_{p+G-1}],
+// Tg upper triangular, built block column by block column from the T_j and the Gram blocks Yg^H Yg:
+//     Tg(0:o_j, o_j:o_j+w_j) = -Tg(0:o_j, 0:o_j) (Yg(:, 0:o_j)^H Y_j) T_j,   Tg(o_j.., o_j..) = T_j.
+// Each group then costs three products with inner dimension sum w_j (or m), last group first.
 template <class T> int bt_he2hb(Sys& s, T* Yb, int ldy, int k) {
-  const int n = s.n, b = s.band_b_used;
+  const int n = s.n, pw = s.q1_pw, off = s.q1_off, nrefl = s.q1_nrefl;
   T* V1 = (T*)s.V1;
   T* T1 = (T*)s.T1;
   const int np = s.nsbr_panels;
   if (np <= 0) return 0;
   const int G = std::min(4, np);
-  const int gb = G * b;                   // <= 4 b
+  const int gb = G * pw;                  // <= 4 b
   T* Wk = (T*)s.Pn;                       // gb x k  (the panel buffers: 8 b n elements)
   T* Wk2 = Wk + (size_t)gb * k;           // gb x k
   T* Tg = (T*)s.btg;                      // gb x gb
   T* Gg = Tg + (size_t)gb * gb;           // gb x gb Gram blocks
-  T* Xg = Gg + (size_t)gb * gb;           // gb x b
+  T* Xg = Gg + (size_t)gb * gb;           // gb x pw
   const T one = from_re<T>(1.0), mone = from_re<T>(-1.0), zero = zero_<T>();
+  auto width = [&](int p) { return std::min(pw, nrefl - p * pw); };
   const int ngroups = (np + G - 1) / G;
   for (int q = ngroups - 1; q >= 0; --q) {
-    const int p0 = q * G, pc = std::min(G, np - p0), w = pc * b;
-    const int j0 = p0 * b, r0 = j0 + b, m = n - r0;
+    const int p0 = q * G, pc = std::min(G, np - p0);
+    int w = 0;
+    for (int j = 0; j < pc; ++j) w += width(p0 + j);
+    const int j0 = p0 * pw, r0 = j0 + off, m = n - r0;
+    if (m <= 0 || w <= 0) continue;
     const T* Yg = V1 + r0 + (long long)j0 * n;  // m x w
     // Tg: block column 0 = T_p0; block column j from the Gram blocks
     GEV_CUDA_TRY(cudaMemset2DAsync(Tg, sizeof(T) * gb, 0, sizeof(T) * w, w, s.stream));
-    GEV_TRY(copy2d<T>(s, b, b, T1 + (long long)j0 * b, b, Tg, gb));
+    GEV_TRY(copy2d<T>(s, width(p0), width(p0), T1 + (size_t)p0 * pw * pw, pw, Tg, gb));
     if (pc > 1) {
       GemmP<T> g = gp<T>(w, w, m, 2, 0, one, Yg, n, Yg, n, zero, Gg, gb);  // Gram Yg^H Yg
       gemm(s, g);
       for (int j = 1; j < pc; ++j) {
-        const T* Tj = T1 + (long long)(j0 + j * b) * b;
-        g = gp<T>(j * b, b, b, 0, 0, one, Gg + (size_t)j * b * gb, gb, Tj, b, zero, Xg, gb);  // X = G(0:jb, j) T_j
+        const int oj = j * pw, wj = width(p0 + j);
+        const T* Tj = T1 + (size_t)(p0 + j) * pw * pw;
+        g = gp<T>(oj, wj, wj, 0, 0, one, Gg + (size_t)oj * gb, gb, Tj, pw, zero, Xg, gb);  // X = G(0:oj, j) T_j
         g.tri_b = 2;
         gemm(s, g);
-        g = gp<T>(j * b, b, j * b, 0, 0, mone, Tg, gb, Xg, gb, zero, Tg + (size_t)j * b * gb, gb);
-        g.tri_a = 2;                                                   // Tg(0:jb, j) = -Tg(0:jb, 0:jb) X
+        g = gp<T>(oj, wj, oj, 0, 0, mone, Tg, gb, Xg, gb, zero, Tg + (size_t)oj * gb, gb);
+        g.tri_a = 2;                                                   // Tg(0:oj, j) = -Tg(0:oj, 0:oj) X
         gemm(s, g);
-        GEV_TRY(copy2d<T>(s, b, b, Tj, b, Tg + j * b + (size_t)j * b * gb, gb));
+        GEV_TRY(copy2d<T>(s, wj, wj, Tj, pw, Tg + oj + (size_t)oj * gb, gb));
       }
     }
     T* Ysub = Yb + r0;
@@ -348,6 +359,7 @@ template <class T> int bt_he2hb(Sys& s, T* Yb, int ldy, int k) {
 
 // Step 6 ("Back"): Y = Q1 Q2 D Z.
 template <class T> int back(Sys& s, const double* Z, int ldz, int k, T* Y, int ldy) {
+  if (s.one_stage_used) return back_td<T>(s, Z, ldz, k, Y, ldy);
   GEV_TRY(bt_hb2st<T>(s, Z, ldz, k, Y, ldy));
   GEV_TRY(bt_he2hb<T>(s, Y, ldy, k));
   return 0;

@@ -32,7 +32,7 @@ SYMBOLS = [
     "gev_default_opts", "gev_setup", "gev_solve", "gev_reuse_factor", "gev_free",
     "gev_workspace_bytes", "gev_strerror", "gev_step_potrf", "gev_step_trtri", "gev_step_hegst",
     "gev_step_he2hb", "gev_step_hb2st", "gev_step_stedc", "gev_step_back", "gev_step_mult",
-    "gev_density", "gev_check", "gev_solve_reduced",
+    "gev_density", "gev_check", "gev_solve_reduced", "gev_step_he2td",
 ]
 
 
@@ -51,7 +51,7 @@ class Opts(ctypes.Structure):
                 ("timing", ctypes.c_int), ("fp64_emulation", ctypes.c_int),
                 ("refine_rr_only", ctypes.c_int), ("fp32_products", ctypes.c_int),
                 ("wait_limit", ctypes.c_int), ("check", ctypes.c_int), ("debug_stall", ctypes.c_int),
-                ("rr_band_b", ctypes.c_int)]
+                ("rr_band_b", ctypes.c_int), ("one_stage", ctypes.c_int)]
 
 
 class Report(ctypes.Structure):
@@ -98,6 +98,7 @@ def lib() -> ctypes.CDLL:
         L.gev_step_trtri.argtypes = [vp, vp, i]
         L.gev_step_hegst.argtypes = [vp, vp, i, vp, i, vp, i]
         L.gev_step_he2hb.argtypes = [vp, vp, i, i, ip]
+        L.gev_step_he2td.argtypes = [vp, vp, i, vp, vp]
         L.gev_step_hb2st.argtypes = [vp, vp, vp]
         L.gev_step_stedc.argtypes = [vp, vp, vp, i, vp, vp, i, ip]
         L.gev_step_back.argtypes = [vp, vp, i, i, vp, i]
@@ -152,7 +153,8 @@ class Solver:
                  band_b: int = 0, panel_nb: int = 0, timing: int = 0, stream=None,
                  workspace_limit: int = 0, refine_tol: float = 0.0, refine_max_iter: int = 0,
                  fp64_emulation: int = -1, refine_rr_only: int = 0, fp32_products: int = -1,
-                 wait_limit: int = 0, check: bool = False, debug_stall: bool = False, rr_band_b: int = 0):
+                 wait_limit: int = 0, check: bool = False, debug_stall: bool = False, rr_band_b: int = 0,
+                 one_stage: bool = False):
         import torch
 
         if not torch.cuda.is_available():
@@ -187,6 +189,7 @@ class Solver:
         o.check = 1 if check else 0
         o.debug_stall = 1 if debug_stall else 0
         o.rr_band_b = int(rr_band_b)
+        o.one_stage = 1 if one_stage else 0
         self.opts = o
         h = ctypes.c_void_p()
         _check(lib().gev_setup(ctypes.byref(h), n, GEV_C128 if complex_ else GEV_F64, ctypes.byref(o)),
@@ -320,6 +323,15 @@ class Solver:
         used = ctypes.c_int(0)
         _check(lib().gev_step_he2hb(self.h, _ptr(Ab), self.n, b, ctypes.byref(used)), "gev_step_he2hb")
         return used.value
+
+    def he2td(self, Ab):
+        """One-stage tridiagonalisation of the Hermitian Ab (column-major, overwritten): (d, e)."""
+        import torch
+
+        d = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        e = torch.empty(max(self.n - 1, 1), dtype=torch.float64, device=self.device)
+        _check(lib().gev_step_he2td(self.h, _ptr(Ab), self.n, _ptr(d), _ptr(e)), "gev_step_he2td")
+        return d, e[: self.n - 1]
 
     def hb2st(self):
         import torch
