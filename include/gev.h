@@ -102,12 +102,19 @@ typedef struct {
                             sets, so its bounded wait expires (GEV_ERR_TIMEOUT); 0 = off */
   int rr_band_b;         /* mixed form: band width of the FP64 Rayleigh-Ritz solve of the refinement
                             (16, 32 or 64; 0 = automatic: 64) */
-  int one_stage;         /* 1: one-stage Householder tridiagonalisation (the ELPA1 form of the section
-                            "Usability and Tutorials", reported there as the faster GPU choice when all
-                            or most eigenpairs are wanted) with a single back-transform, instead of
-                            full -> band, bulge chasing and two back-transforms; plain form only
-                            (GEV_MIXED returns GEV_ERR_UNSUPPORTED).  Panel width = the band width
-                            option (16, 32 or 64).  0 = two-stage (default) */
+  int one_stage;         /* tridiagonalisation route.  1: one-stage Householder reduction (the ELPA1 form
+                            of the section "Usability and Tutorials", reported there as the faster GPU
+                            choice when all or most eigenpairs are wanted) with a single
+                            back-transform, in FP64 (plain form) or FP32 (real mixed form; the complex
+                            mixed form returns GEV_ERR_UNSUPPORTED); panel width = the band width.
+                            2: two-stage (full -> band, bulge chasing, two back-transforms).
+                            0 = automatic (default): plain form one-stage for 2048 <= n <= 8192, or for
+                            n >= 2048 with k >= n/2 (where it measured faster on GB300: its
+                            matrix-vector products are bound by the FP64 pipe, the two-stage route's
+                            products run on the tensor cores), else two-stage; mixed forms two-stage */
+  int rr_one_stage;      /* mixed form, the FP64 Rayleigh-Ritz solve of the refinement (all k pairs of
+                            a k x k pencil): 1 = one-stage, 2 = two-stage, 0 = automatic (one-stage for
+                            k >= 2048) */
 } gev_opts;
 
 typedef struct {

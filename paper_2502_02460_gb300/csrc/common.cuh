@@ -364,6 +364,12 @@ template <class T> int hb2st(Sys& s, double* d, double* e);
 int stedc(Sys& s, const double* d, const double* e, int k, double* w, double* Z, int ldz, int* deflated);
 template <class T> int back(Sys& s, const double* Z, int ldz, int k, T* Y, int ldy);
 template <class T> int bt_he2hb(Sys& s, T* Y, int ldy, int k);
+// the route of a plain-form solve of order n for k pairs (gev_opts.one_stage: 1 / 2 forced, 0 automatic)
+inline bool one_stage_for(int opt, int n, int k) {
+  if (opt == 1) return true;
+  if (opt == 2) return false;
+  return n >= 2048 && (n <= 8192 || 2 * (long long)k >= n);
+}
 // one-stage Householder tridiagonalisation into s.d / s.e, and Y = Q Z for it (td1.cu)
 template <class T> int he2td(Sys& s, T* A, int lda);
 template <class T> int back_td(Sys& s, const double* Z, int ldz, int k, T* Y, int ldy);

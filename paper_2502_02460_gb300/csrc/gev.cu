@@ -262,7 +262,7 @@ int gev_solve(gev_sys* h, const void* H, int ldh, const void* S, int lds, int k,
   if (!S && !(s.reuse && s.have_factor && s.factor_kind == 0)) return GEV_ERR_REUSE_WITHOUT_FACTOR;
   if (cudaSetDevice(s.opts.device) != cudaSuccess) return GEV_ERR_CUDA;
   if (rep) std::memset(rep, 0, sizeof(*rep));
-  if (s.opts.one_stage && s.opts.prec == GEV_MIXED) return GEV_ERR_UNSUPPORTED;
+  if (s.opts.one_stage == 1 && s.opts.prec == GEV_MIXED && s.dtype == GEV_C128) return GEV_ERR_UNSUPPORTED;
   int r;
   if (s.opts.prec == GEV_MIXED && s.dtype == GEV_C128)
     r = solve_mixed_cx(s, (const zd*)H, ldh, (const zd*)S, lds, k, evals, (zd*)C, ldc, rep);
@@ -552,7 +552,7 @@ template <class T> int solve_t(Sys& s, const T* H, int ldh, const T* S, int lds,
   GEV_TRY(hegst<T>(s, H, ldh, X, n, A, n));
   s.have_factor = true;
   s.factor_kind = 0;
-  const bool one = s.opts.one_stage != 0;
+  const bool one = one_stage_for(s.opts.one_stage, n, k);
   // steps 4a / 4b: two-stage tridiagonalisation (or the one-stage reduction, timed as "to_tridiag")
   mark(GEV_STEP_TO_BAND);
   if (!one) GEV_TRY(he2hb<T>(s, A, n, s.b));

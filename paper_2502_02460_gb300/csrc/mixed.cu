@@ -316,12 +316,15 @@ int solve_mixed(Sys& s, const double* H, int ldh, const double* S, int lds, int 
   s.have_factor = true;
   s.factor_kind = 0;
   // ---- FP32 reduction of A32 = fl32(A); all n eigenvectors (the refinement uses the complement)
+  // (one-stage option: Householder tridiagonalisation of A32 directly, timed as "to_tridiag")
+  const bool one = s.opts.one_stage == 1;  // automatic: two-stage (measured faster in FP32 at n = 16384)
   mark(GEV_STEP_TO_BAND);
   float* A32 = (float*)s.W1;
   GEV_TRY((convert2d<double, float>(s, n, n, A, n, A32, n)));
-  GEV_TRY(he2hb<float>(s, A32, n, s.b));
+  if (!one) GEV_TRY(he2hb<float>(s, A32, n, s.b));
   mark(GEV_STEP_TO_TRIDIAG);
-  GEV_TRY(hb2st<float>(s, s.d, s.e));
+  if (one) GEV_TRY(he2td<float>(s, A32, n));
+  else GEV_TRY(hb2st<float>(s, s.d, s.e));
   GEV_TRY(stop_on_timeout(s));
   mark(GEV_STEP_SOLVE);
   s.dc_lowp = 1;
@@ -331,10 +334,11 @@ int solve_mixed(Sys& s, const double* H, int ldh, const double* S, int lds, int 
   mark(GEV_STEP_BACK_TRIDIAG);
   float* Y32 = (float*)s.Yk;
   s.z_unit = true;  // the divide-and-conquer eigenvectors
-  GEV_TRY(bt_hb2st<float>(s, s.Zk, n, n, Y32, n));
+  if (one) GEV_TRY(back_td<float>(s, s.Zk, n, n, Y32, n));
+  else GEV_TRY(bt_hb2st<float>(s, s.Zk, n, n, Y32, n));
   s.z_unit = false;
   mark(GEV_STEP_BACK_BAND);
-  GEV_TRY(bt_he2hb<float>(s, Y32, n, n));
+  if (!one) GEV_TRY(bt_he2hb<float>(s, Y32, n, n));
   // ---- FP64 refinement of the k lowest pairs
   mark(GEV_STEP_REFINE);
   // buffers (all free or dedicated at this point; every one large enough also for k = n)
@@ -375,7 +379,7 @@ int solve_mixed(Sys& s, const double* H, int ldh, const double* S, int lds, int 
     o.band_b = rr_band(s.opts.rr_band_b, k);
     o.fp64_emulation = s.emu_fp64;  // the Ritz pencil's products use the same FP64 engine
     o.check = 0;
-    o.one_stage = 0;
+    o.one_stage = (s.opts.rr_one_stage == 1 || (s.opts.rr_one_stage == 0 && k >= 2048)) ? 1 : 2;
     o.debug_stall = 0;
     gev_sys* h = nullptr;
     const int rc = gev_setup(&h, k, GEV_F64, &o);
@@ -600,7 +604,7 @@ int solve_mixed_cx(Sys& s, const zd* H, int ldh, const zd* S, int lds, int k, do
     o.band_b = rr_band(s.opts.rr_band_b, k);
     o.fp64_emulation = s.emu_fp64;
     o.check = 0;
-    o.one_stage = 0;
+    o.one_stage = (s.opts.rr_one_stage == 1 || (s.opts.rr_one_stage == 0 && k >= 2048)) ? 1 : 2;
     o.debug_stall = 0;
     gev_sys* h = nullptr;
     const int rc = gev_setup(&h, k, GEV_C128, &o);

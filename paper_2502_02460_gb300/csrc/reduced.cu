@@ -51,7 +51,7 @@ int solve_reduced(Sys& s, const T* H, int ldh, const T* S, int lds, double delta
     // 1. all eigenpairs of S
     GEV_TRY(copy_lower<T>(s, n, S, lds, A, n));
     GEV_TRY(mirror_lower<T>(s, n, A, n));
-    if (s.opts.one_stage) {
+    if (one_stage_for(s.opts.one_stage, n, n)) {  // all n pairs of S
       GEV_TRY(he2td<T>(s, A, n));
     } else {
       GEV_TRY(he2hb<T>(s, A, n, s.b));
@@ -127,7 +127,7 @@ int solve_reduced(Sys& s, const T* H, int ldh, const T* S, int lds, double delta
   GEV_TRY(reset_status(u));
   T* Au = (T*)u.A;
   GEV_TRY(copy2d<T>(u, m, m, A, m, Au, m));
-  if (u.opts.one_stage) {
+  if (one_stage_for(u.opts.one_stage, m, k)) {
     GEV_TRY(he2td<T>(u, Au, m));
   } else {
     GEV_TRY(he2hb<T>(u, Au, m, u.b));

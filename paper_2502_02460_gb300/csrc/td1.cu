@@ -58,6 +58,7 @@ template <class T> struct TdArgs {
   GridBar gb;
 };
 
+__device__ __forceinline__ float shx(float v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
 __device__ __forceinline__ double shx(double v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
 __device__ __forceinline__ zd shx(zd v, int m) {
   return make_zd(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
@@ -65,6 +66,22 @@ __device__ __forceinline__ zd shx(zd v, int m) {
 template <class T> __device__ __forceinline__ T group_sum(T v, int width) {
   for (int m = width >> 1; m > 0; m >>= 1) v += shx(v, m);
   return v;
+}
+
+// sum of f(i) over i = start, start + step, ... < end with four independent accumulators, so that
+// four loads are in flight (the terms are L2 reads); the order is fixed by the arguments
+template <class T, class F> __device__ __forceinline__ T ssum(int start, int end, int step, F f) {
+  T a0 = zero_<T>(), a1 = zero_<T>(), a2 = zero_<T>(), a3 = zero_<T>();
+  int i = start;
+  for (; i + 3 * step < end; i += 4 * step) {
+    const T x0 = f(i), x1 = f(i + step), x2 = f(i + 2 * step), x3 = f(i + 3 * step);
+    a0 += x0;
+    a1 += x1;
+    a2 += x2;
+    a3 += x3;
+  }
+  for (; i < end; i += step) a0 += f(i);
+  return (a0 + a1) + (a2 + a3);
 }
 
 // block-wide sum in a fixed order; the result is returned to every thread
@@ -146,10 +163,10 @@ __global__ void __launch_bounds__(NT, 2) k_td_panel(TdArgs<T> a) {
         const bool ok = i < rhi;
         T acc = zero_<T>();
         if (ok)
-          for (int l = lane; l < c; l += tpr) {
+          acc = ssum<T>(lane, c, tpr, [&](int l) {
             const long long o = i + (long long)l * ldw;
-            acc += ldcg_(&Vp[o]) * s_wj[l] + ldcg_(&Wp[o]) * s_vj[l];
-          }
+            return ldcg_(&Vp[o]) * s_wj[l] + ldcg_(&Wp[o]) * s_vj[l];
+          });
         acc = group_sum(acc, tpr);
         if (ok && lane == 0) {
           T* pa = &a.A[i + (long long)j * lda];
@@ -210,31 +227,56 @@ __global__ void __launch_bounds__(NT, 2) k_td_panel(TdArgs<T> a) {
     const int t0 = (j + 1) / TS;
     const int ntile = (n + TS - 1) / TS - t0;
     const long long ntt = (long long)ntile * (ntile + 1) / 2;
-    for (long long t = g; t < ntt; t += G) {
-      int I = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    // tile t -> (I, L) with t = I (I + 1) / 2 + L
+    // (the first guess in FP32: FP64 arithmetic is scarce on this part and t < 2^24)
+    auto tile_of = [&](long long t, int& I, int& L) {
+      I = (int)((__fsqrt_rn(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
       while ((long long)I * (I + 1) / 2 > t) --I;
       while ((long long)(I + 1) * (I + 2) / 2 <= t) ++I;
-      const int L = (int)(t - (long long)I * (I + 1) / 2);
+      L = (int)(t - (long long)I * (I + 1) / 2);
+    };
+    // this thread's 16 entries of tile (I, L): row r = tid % 64, columns 16 q .. 16 q + 15
+    T nx[16];
+    auto load_tile = [&](int I, int L) {
+      const int r = tid & (TS - 1), q = tid >> 6;
+      const int rb = (t0 + I) * TS, cb = (t0 + L) * TS, row = rb + r;
+      const bool diag = (I == L), rok = row > j && row < n;
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const int l = q * 16 + k, col = cb + l;
+        T val = zero_<T>();
+        if (rok && col > j && col < n && (!diag || r >= l)) {
+          val = a.A[row + (long long)col * lda];
+          if (diag && r == l) val = from_re<T>(re_(val));
+        }
+        nx[k] = val;
+      }
+    };
+    const int gt = g - a.npd, Gt = G - a.npd;  // tile blocks: g >= npd
+    if (gt >= 0 && gt < ntt) {
+      int I, L;
+      tile_of(gt, I, L);
+      load_tile(I, L);
+    }
+    // the next tile's entries are loaded into registers while this one is multiplied from shared memory
+    for (long long t = gt; gt >= 0 && t < ntt; t += Gt) {
+      int I, L;
+      tile_of(t, I, L);
       const int rb = (t0 + I) * TS, cb = (t0 + L) * TS;
       const bool diag = (I == L);
       {
         const int r = tid & (TS - 1), q = tid >> 6;
-        const int row = rb + r;
-        const bool rok = row > j && row < n;
-#pragma unroll 4
-        for (int k = 0; k < 16; ++k) {
-          const int l = q * 16 + k, col = cb + l;
-          T val = zero_<T>();
-          if (rok && col > j && col < n && (!diag || r >= l)) {
-            val = a.A[row + (long long)col * lda];
-            if (diag && r == l) val = from_re<T>(re_(val));
-          }
-          As[r + l * TLD] = val;
-        }
+#pragma unroll
+        for (int k = 0; k < 16; ++k) As[r + (q * 16 + k) * TLD] = nx[k];
         if (tid < TS) vL[tid] = vfun(cb + tid);
         else if (tid < 2 * TS) vI[tid - TS] = vfun(rb + tid - TS);
       }
       __syncthreads();
+      if (t + Gt < ntt) {
+        int I2, L2;
+        tile_of(t + Gt, I2, L2);
+        load_tile(I2, L2);
+      }
       {
         const int x = tid & (TS - 1), q = tid >> 6;
         T sd = zero_<T>(), st = zero_<T>();
@@ -248,6 +290,8 @@ __global__ void __launch_bounds__(NT, 2) k_td_panel(TdArgs<T> a) {
         redT[q * TS + x] = st;
       }
       __syncthreads();
+      // (the next iteration's shared-memory stores touch As, vI and vL only; its reduction
+      // buffers are written after its first barrier, when every thread has left this one)
       if (tid < TS) {
         T o = redD[tid] + redD[TS + tid] + redD[2 * TS + tid] + redD[3 * TS + tid];
         if (diag) o += redT[tid] + redT[TS + tid] + redT[2 * TS + tid] + redT[3 * TS + tid];
@@ -256,21 +300,37 @@ __global__ void __launch_bounds__(NT, 2) k_td_panel(TdArgs<T> a) {
         const int x = tid - TS;
         a.slots[((long long)L * ntile + I) * TS + x] = redT[x] + redT[TS + x] + redT[2 * TS + x] + redT[3 * TS + x];
       }
-      __syncthreads();
     }
-    // V^H v and W^H v over rows [j+1, n), blocks g < npd, one warp per value, lanes over rows
+    __syncthreads();
+    // V^H v and W^H v over rows [j+1, n) on the npd dot blocks (no tiles): warp w sums values
+    // 16 w .. 16 w + 15 (value u < c: column u of V, else column u - c of W), lanes over rows, the
+    // sixteen column loads of a row in flight together
     if (g < a.npd && c > 0) {
       const int m = n - (j + 1);
       const int Rd = (m + a.npd - 1) / a.npd;
       const int lo = j + 1 + g * Rd, hi = min(n, lo + Rd);
-      const int lane = tid & 31, wid = tid >> 5;
-      for (int val = wid; val < 2 * c; val += NT / 32) {
-        const int l = val % c;
-        const T* col = (val < c ? Vp : Wp) + (long long)l * ldw;
-        T acc = zero_<T>();
-        for (int i = lo + lane; i < hi; i += 32) acc += cmul(ldcg_(&col[i]), vfun(i));
-        acc = group_sum(acc, 32);
-        if (lane == 0) a.dparts[(long long)g * 2 * nb + (val < c ? l : nb + l)] = acc;
+      const int lane = tid & 31, vb = (tid >> 5) * 16;
+      if (vb < 2 * c) {
+        T acc[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) acc[u] = zero_<T>();
+        for (int i = lo + lane; i < hi; i += 32) {
+          const T vi = vfun(i);
+#pragma unroll
+          for (int u = 0; u < 16; ++u) {
+            const int val = vb + u;
+            if (val < 2 * c) {
+              const T* col = val < c ? Vp + (long long)val * ldw : Wp + (long long)(val - c) * ldw;
+              acc[u] += cmul(ldcg_(&col[i]), vi);
+            }
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const int val = vb + u;
+          const T r = group_sum(acc[u], 32);
+          if (lane == 0 && val < 2 * c) a.dparts[(long long)g * 2 * nb + (val < c ? val : nb + val - c)] = r;
+        }
       }
     }
     if (!grid_sync(a.gb, 202)) return;
@@ -278,25 +338,13 @@ __global__ void __launch_bounds__(NT, 2) k_td_panel(TdArgs<T> a) {
     for (int l = tid; l < 2 * c; l += NT) {
       const int ll = l % c;
       const int off = l < c ? ll : nb + ll;
-      T s = zero_<T>();
-      for (int q = 0; q < a.npd; ++q) s += ldcg_(&a.dparts[(long long)q * 2 * nb + off]);
+      const T s = ssum<T>(0, a.npd, 1, [&](int q) { return ldcg_(&a.dparts[(long long)q * 2 * nb + off]); });
       if (l < c) s_vhv[ll] = s;
       else s_whv[ll] = s;
     }
     __syncthreads();
-    if (g == 0) {
-      for (int i = tid; i < nb; i += NT) {
-        T val = zero_<T>();
-        if (i < c) {
-          T acc = zero_<T>();
-          for (int l = i; l < c; ++l) acc += a.Tp[i + (long long)l * nb] * s_vhv[l];
-          val = -(tau * acc);
-        } else if (i == c) {
-          val = tau;
-        }
-        a.Tp[i + (long long)c * nb] = val;
-      }
-    }
+    if (g == 0)  // column c of T, raw: (V^H v_c above the diagonal, tau_c on it), finished at the end
+      for (int i = tid; i < nb; i += NT) a.Tp[i + (long long)c * nb] = i < c ? s_vhv[i] : (i == c ? tau : zero_<T>());
     T dotp = zero_<T>();
     {
       const int r0 = max(rlo, j + 1), nr = max(0, rhi - r0);
@@ -308,11 +356,11 @@ __global__ void __launch_bounds__(NT, 2) k_td_panel(TdArgs<T> a) {
         if (ok) {
           const int Ri = i / TS - t0, r = i % TS;
           const T* sl = a.slots + (long long)Ri * ntile * TS + r;
-          for (int X = lane; X < ntile; X += tpr) acc += ldcg_(&sl[(long long)X * TS]);
-          for (int l = lane; l < c; l += tpr) {
+          acc = ssum<T>(lane, ntile, tpr, [&](int X) { return ldcg_(&sl[(long long)X * TS]); });
+          acc -= ssum<T>(lane, c, tpr, [&](int l) {
             const long long o = i + (long long)l * ldw;
-            acc -= ldcg_(&Vp[o]) * s_whv[l] + ldcg_(&Wp[o]) * s_vhv[l];
-          }
+            return ldcg_(&Vp[o]) * s_whv[l] + ldcg_(&Wp[o]) * s_vhv[l];
+          });
         }
         acc = group_sum(acc, tpr);
         if (ok && lane == 0) {
@@ -344,6 +392,29 @@ __global__ void __launch_bounds__(NT, 2) k_td_panel(TdArgs<T> a) {
         Wq[o] = w;
       }
     }
+  }
+  // the panel's compact-WY factor from its raw columns (forward accumulation):
+  //   T(0:c, c) = -tau_c T(0:c, 0:c) (V(:, 0:c)^H v_c),   T(c, c) = tau_c
+  if (g == 0) {
+    const int nr = min(a.pw, n - 1 - j0);  // reflectors in this panel
+    T* Ts = As;                            // nb x nb in shared memory (ld nb)
+    for (int q = tid; q < nb * nb; q += NT) {
+      const int i = q % nb, cc = q / nb;
+      Ts[q] = (i < nr && cc < nr) ? a.Tp[i + (long long)cc * nb] : zero_<T>();
+    }
+    __syncthreads();
+    for (int cc = 1; cc < nr; ++cc) {
+      if (tid < cc) vI[tid] = Ts[tid + cc * nb];
+      __syncthreads();
+      const T tc = Ts[cc + cc * nb];
+      if (tid < cc) {
+        T acc = zero_<T>();
+        for (int l = tid; l < cc; ++l) acc += Ts[tid + l * nb] * vI[l];
+        Ts[tid + cc * nb] = -(tc * acc);
+      }
+      __syncthreads();
+    }
+    for (int q = tid; q < nb * nb; q += NT) a.Tp[q] = Ts[q];
   }
 }
 
@@ -393,8 +464,9 @@ template <class T> int he2td(Sys& s, T* A, int lda) {
   a.nparts = (double*)pw_base;                       // gmax doubles
   a.aparts = (T*)(pw_base + 2048 * 8);               // gmax values
   a.piv = (T*)(pw_base + 2048 * 8 + 2048 * 16);
-  a.dparts = (T*)(pw_base + 2048 * 8 + 2048 * 16 + 256);  // 32 x 2nb values
-  if ((size_t)2048 * 8 + 2048 * 16 + 256 + (size_t)32 * 2 * nb * sizeof(T) > s.panelws_bytes || gmax > 2048)
+  a.dparts = (T*)(pw_base + 2048 * 8 + 2048 * 16 + 256);  // 16 x 2nb values
+  if ((size_t)2048 * 8 + 2048 * 16 + 256 + (size_t)16 * 2 * nb * sizeof(T) > s.panelws_bytes || gmax > 2048 ||
+      gmax < 2)
     return GEV_ERR_UNSUPPORTED;
   a.gb = GridBar{(unsigned*)&s.status[ST_BARRIER_CNT], (unsigned*)&s.status[ST_BARRIER_GEN], s.status,
                  &s.status[ST_ABORT]};
@@ -403,10 +475,12 @@ template <class T> int he2td(Sys& s, T* A, int lda) {
     const int pw = std::min(nb, n - j0);
     const long long nt0 = (long long)((n + TS - 1) / TS - (j0 + 1) / TS);
     const long long ntt = nt0 * (nt0 + 1) / 2;
-    int G = (int)std::min<long long>(gmax, std::max<long long>(ntt, 1));
+    // dot blocks (V^H v, W^H v over ~256 rows each, at most 16) beside the tile blocks
+    const int npd = std::max(1, std::min(16, (n - j0) / 256));
+    const int G = npd + (int)std::min<long long>(gmax - npd, std::max<long long>(ntt, 1));
     a.j0 = j0;
     a.pw = pw;
-    a.npd = std::min(G, 32);
+    a.npd = npd;
     a.Tp = (T*)s.T1 + (size_t)(j0 / nb) * nb * nb;
     GEV_CUDA_TRY(cudaMemsetAsync(&s.status[ST_BARRIER_CNT], 0, 2 * sizeof(int), s.stream));
     void* args[] = {&a};
@@ -442,8 +516,10 @@ template <class T> int back_td(Sys& s, const double* Z, int ldz, int k, T* Y, in
   return bt_he2hb<T>(s, Y, ldy, k);
 }
 
+template int he2td<float>(Sys&, float*, int);
 template int he2td<double>(Sys&, double*, int);
 template int he2td<zd>(Sys&, zd*, int);
+template int back_td<float>(Sys&, const double*, int, int, float*, int);
 template int back_td<double>(Sys&, const double*, int, int, double*, int);
 template int back_td<zd>(Sys&, const double*, int, int, zd*, int);
 

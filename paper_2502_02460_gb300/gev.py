@@ -51,7 +51,8 @@ class Opts(ctypes.Structure):
                 ("timing", ctypes.c_int), ("fp64_emulation", ctypes.c_int),
                 ("refine_rr_only", ctypes.c_int), ("fp32_products", ctypes.c_int),
                 ("wait_limit", ctypes.c_int), ("check", ctypes.c_int), ("debug_stall", ctypes.c_int),
-                ("rr_band_b", ctypes.c_int), ("one_stage", ctypes.c_int)]
+                ("rr_band_b", ctypes.c_int), ("one_stage", ctypes.c_int),
+                ("rr_one_stage", ctypes.c_int)]
 
 
 class Report(ctypes.Structure):
@@ -154,7 +155,7 @@ class Solver:
                  workspace_limit: int = 0, refine_tol: float = 0.0, refine_max_iter: int = 0,
                  fp64_emulation: int = -1, refine_rr_only: int = 0, fp32_products: int = -1,
                  wait_limit: int = 0, check: bool = False, debug_stall: bool = False, rr_band_b: int = 0,
-                 one_stage: bool = False):
+                 one_stage=None, rr_one_stage=None):
         import torch
 
         if not torch.cuda.is_available():
@@ -189,7 +190,9 @@ class Solver:
         o.check = 1 if check else 0
         o.debug_stall = 1 if debug_stall else 0
         o.rr_band_b = int(rr_band_b)
-        o.one_stage = 1 if one_stage else 0
+        # tridiagonalisation route: None = automatic, True = one-stage, False = two-stage
+        o.one_stage = 0 if one_stage is None else (1 if one_stage else 2)
+        o.rr_one_stage = 0 if rr_one_stage is None else (1 if rr_one_stage else 2)
         self.opts = o
         h = ctypes.c_void_p()
         _check(lib().gev_setup(ctypes.byref(h), n, GEV_C128 if complex_ else GEV_F64, ctypes.byref(o)),

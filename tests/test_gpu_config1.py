@@ -51,9 +51,10 @@ def check_report(p, w, C, rep, r_oracle, o_oracle):
     assert abs(rep["ortho"] - o_oracle) <= 0.5 * o_oracle + 2e-13, (rep["ortho"], o_oracle)
 
 
-def test_config1_plain_matches_oracle(dev, case):
+@pytest.mark.parametrize("one_stage", [False, True], ids=["two_stage", "one_stage"])
+def test_config1_plain_matches_oracle(dev, case, one_stage):
     p, ref = case
-    w, C, rep = solve(p, dev)
+    w, C, rep = solve(p, dev, one_stage=one_stage)
     r, o = compare_to_oracle(p, w, C, K, ref=ref)
     check_report(p, w, C, rep, r, o)
     assert rep["deflated"] >= 0
@@ -66,9 +67,10 @@ def test_config1_plain_native_products_matches_oracle(dev, case):
     check_report(p, w, C, rep, r, o)
 
 
-def test_config1_mixed_matches_oracle(dev, case):
+@pytest.mark.parametrize("one_stage", [False, True], ids=["fp32_two_stage", "fp32_one_stage"])
+def test_config1_mixed_matches_oracle(dev, case, one_stage):
     p, ref = case
-    w, C, rep = solve(p, dev, mixed=True)
+    w, C, rep = solve(p, dev, mixed=True, one_stage=one_stage)
     assert rep["refine_resid"] <= 1e-11
     r, o = compare_to_oracle(p, w, C, K, resid_bound=1e-11, ref=ref)
     check_report(p, w, C, rep, r, o)

@@ -19,7 +19,7 @@ from tests.pins import norm1
 
 pytestmark = pytest.mark.gpu
 
-GEV_ERR_UNSUPPORTED = 8
+GEV_ERR_UNSUPPORTED = 7
 
 
 @pytest.fixture(scope="module")
@@ -116,16 +116,16 @@ def test_one_stage_is_deterministic_and_agrees_with_two_stage(dev):
         w1, C1 = s.solve_cm(H, S, k)
         w2, C2 = s.solve_cm(H, S, k)
     assert (w1 == w2).all() and (C1 == C2).all()
-    with g.Solver(n, complex_=True, device=dev) as s:
+    with g.Solver(n, complex_=True, device=dev, one_stage=False) as s:
         w3, _ = s.solve_cm(H, S, k)
     assert float((w1 - w3).abs().max()) <= 1e-11 * norm1(p.H)
 
 
-def test_one_stage_with_mixed_form_is_unsupported(dev):
+def test_one_stage_with_complex_mixed_form_is_unsupported(dev):
     g = gv()
     n = 64
-    p = inputs.make_problem(n, 8, seed=1)
-    with g.Solver(n, device=dev, mixed=True, one_stage=True) as s:
+    p = inputs.make_problem(n, 8, seed=1, complex_=True)
+    with g.Solver(n, complex_=True, device=dev, mixed=True, one_stage=True) as s:
         with pytest.raises(g.GevError) as ei:
             s.solve_cm(g.cm_from_numpy(p.H, dev), g.cm_from_numpy(p.S, dev), 8)
     assert ei.value.code == GEV_ERR_UNSUPPORTED
@@ -143,3 +143,17 @@ def test_one_stage_reduced_solve_matches_oracle(dev, cx):
         w, _, mk = s.solve_reduced_cm(g.cm_from_numpy(H, dev), g.cm_from_numpy(S, dev), delta, k)
     assert mk == mo
     assert np.max(np.abs(w.cpu().numpy() - wo)) <= 1e-11 * norm1(H)
+
+
+@pytest.mark.parametrize("n,k,cluster", [(700, 175, False), (1100, 275, True), (1300, 1300, False)])
+def test_one_stage_mixed_matches_oracle(dev, n, k, cluster):
+    """Real mixed form on the FP32 one-stage reduction: the refinement reaches the same bounds."""
+    g = gv()
+    p = inputs.make_problem(n, k, seed=31 + n, cluster=cluster)
+    with g.Solver(n, device=dev, mixed=True, one_stage=True, timing=1) as s:
+        w, Cb = s.solve_cm(g.cm_from_numpy(p.H, dev), g.cm_from_numpy(p.S, dev), k)
+        rep = s.last_report
+        w, C = w.cpu().numpy(), g.numpy_from_cm(Cb)
+    compare_to_oracle(p, w, C, k, resid_bound=1e-11)
+    assert rep["refine_resid"] <= 1e-11
+    assert rep["ms"]["to_band"] < 0.5 and rep["ms"]["back_band"] < 0.5
