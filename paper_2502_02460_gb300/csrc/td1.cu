@@ -39,6 +39,8 @@ constexpr int NT = 256;
 constexpr int TS = 64;   // symv tile
 constexpr int TLD = 65;  // its shared-memory leading dimension
 
+constexpr int STG = TS * TLD + 2 * TS;  // shared-memory elements: the tile and its two 64-entry v segments
+
 template <class T> struct TdArgs {
   int n, j0, pw, nb, npd;
   T* A;
@@ -68,20 +70,25 @@ template <class T> __device__ __forceinline__ T group_sum(T v, int width) {
   return v;
 }
 
-// sum of f(i) over i = start, start + step, ... < end with four independent accumulators, so that
-// four loads are in flight (the terms are L2 reads); the order is fixed by the arguments
-template <class T, class F> __device__ __forceinline__ T ssum(int start, int end, int step, F f) {
-  T a0 = zero_<T>(), a1 = zero_<T>(), a2 = zero_<T>(), a3 = zero_<T>();
+// sum of f(i) over i = start, start + step, ... < end with U independent accumulators, so that U
+// loads are in flight (the terms are L2 reads); the order is fixed by the arguments
+template <class T, int U = 4, class F> __device__ __forceinline__ T ssum(int start, int end, int step, F f) {
+  T acc[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) acc[u] = zero_<T>();
   int i = start;
-  for (; i + 3 * step < end; i += 4 * step) {
-    const T x0 = f(i), x1 = f(i + step), x2 = f(i + 2 * step), x3 = f(i + 3 * step);
-    a0 += x0;
-    a1 += x1;
-    a2 += x2;
-    a3 += x3;
+  for (; i + (U - 1) * step < end; i += U * step) {
+    T x[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) x[u] = f(i + u * step);
+#pragma unroll
+    for (int u = 0; u < U; ++u) acc[u] += x[u];
   }
-  for (; i < end; i += step) a0 += f(i);
-  return (a0 + a1) + (a2 + a3);
+  for (; i < end; i += step) acc[0] += f(i);
+  T t = zero_<T>();
+#pragma unroll
+  for (int u = 0; u < U; ++u) t += acc[u];
+  return t;
 }
 
 // block-wide sum in a fixed order; the result is returned to every thread
@@ -107,10 +114,10 @@ __device__ __forceinline__ int rows_tpr(int nrows) {
 template <class T>
 __global__ void __launch_bounds__(NT, 2) k_td_panel(TdArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  T* As = reinterpret_cast<T*>(smraw);  // TS x TLD tile
+  T* As = reinterpret_cast<T*>(smraw);  // stage 0: TS x TLD tile, then two TS-entry vectors
   T* vI = As + TS * TLD;
   T* vL = vI + TS;
-  T* redD = vL + TS;      // 4 x TS
+  T* redD = As + STG;  // 4 x TS
   T* redT = redD + 4 * TS;
   __shared__ T s_vj[128], s_wj[128];   // pivot row of V and W (conjugated)
   __shared__ T s_vhv[128], s_whv[128]; // V^H v, W^H v
@@ -132,26 +139,37 @@ __global__ void __launch_bounds__(NT, 2) k_td_panel(TdArgs<T> a) {
   for (int c = 0; c < a.pw; ++c) {
     const int j = j0 + c;
     // ================= A: finish W(:, c-1); update column j; norm of x = a(j+2:, j)
-    T wpiv_prev = zero_<T>();
+    // (every load of this phase that does not depend on alpha_{c-1} is issued first, together)
+    T part = zero_<T>(), pivv = zero_<T>(), vjl = zero_<T>(), wjl = zero_<T>();
+    T wfin = zero_<T>(), vfin = zero_<T>();
+    const int ifin = max(rlo, j) + tid;  // this thread's first own row of W(:, c-1)
     if (c > 0) {
-      T part = zero_<T>();
       for (int q = tid; q < G; q += NT) part += ldcg_(&a.aparts[q]);
+      pivv = ldcg_(a.piv);
+      if (ifin < rhi) {
+        const long long o = ifin + (long long)(c - 1) * ldw;
+        wfin = ldcg_(&Wp[o]);
+        vfin = ldcg_(&Vp[o]);
+      }
+    }
+    if (tid < c) {
+      vjl = ldcg_(&Vp[j + (long long)tid * ldw]);
+      if (tid < c - 1) wjl = ldcg_(&Wp[j + (long long)tid * ldw]);
+    }
+    if (c > 0) {
       const T dot = block_sum_all(part, s_red);
-      const double alp = -0.5 * re_(tau_prev * dot);
-      const T alpT = from_re<T>(alp);
-      for (int i = max(rlo, j) + tid; i < rhi; i += NT) {
+      const T alpT = from_re<T>(-0.5 * re_(tau_prev * dot));
+      for (int i = ifin; i < rhi; i += NT) {
         const long long o = i + (long long)(c - 1) * ldw;
-        const T w = ldcg_(&Wp[o]) + alpT * ldcg_(&Vp[o]);
+        const T w = (i == ifin ? wfin : ldcg_(&Wp[o])) + alpT * (i == ifin ? vfin : ldcg_(&Vp[o]));
         Wp[o] = w;
         Wq[o] = w;
       }
-      wpiv_prev = ldcg_(a.piv) + alpT;  // v_{c-1}(j) = 1
+      if (tid == c - 1) wjl = pivv + alpT;  // v_{c-1}(j) = 1
     }
-    for (int l = tid; l < c; l += NT) {
-      const T vjl = ldcg_(&Vp[j + (long long)l * ldw]);
-      const T wjl = (l == c - 1) ? wpiv_prev : ldcg_(&Wp[j + (long long)l * ldw]);
-      s_vj[l] = conj_(vjl);
-      s_wj[l] = conj_(wjl);
+    if (tid < c) {
+      s_vj[tid] = conj_(vjl);
+      s_wj[tid] = conj_(wjl);
     }
     __syncthreads();
     double nrm = 0.0;
@@ -235,63 +253,26 @@ __global__ void __launch_bounds__(NT, 2) k_td_panel(TdArgs<T> a) {
       while ((long long)(I + 1) * (I + 2) / 2 <= t) ++I;
       L = (int)(t - (long long)I * (I + 1) / 2);
     };
-    // this thread's 16 entries of tile (I, L): row r = tid % 64, columns 16 q .. 16 q + 15
-    T nx[16];
-    auto load_tile = [&](int I, int L) {
-      const int r = tid & (TS - 1), q = tid >> 6;
-      const int rb = (t0 + I) * TS, cb = (t0 + L) * TS, row = rb + r;
-      const bool diag = (I == L), rok = row > j && row < n;
-#pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        const int l = q * 16 + k, col = cb + l;
-        T val = zero_<T>();
-        if (rok && col > j && col < n && (!diag || r >= l)) {
-          val = a.A[row + (long long)col * lda];
-          if (diag && r == l) val = from_re<T>(re_(val));
-        }
-        nx[k] = val;
-      }
-    };
     const int gt = g - a.npd, Gt = G - a.npd;  // tile blocks: g >= npd
-    if (gt >= 0 && gt < ntt) {
-      int I, L;
-      tile_of(gt, I, L);
-      load_tile(I, L);
-    }
-    // the next tile's entries are loaded into registers while this one is multiplied from shared memory
-    for (long long t = gt; gt >= 0 && t < ntt; t += Gt) {
-      int I, L;
-      tile_of(t, I, L);
-      const int rb = (t0 + I) * TS, cb = (t0 + L) * TS;
+    // the tile's products from shared memory (stage base Ab, v_L / v_I in vl / vi); partial sums to
+    // the two slots
+    auto tile_products = [&](const T* Ab, const T* vl, const T* vi, int I, int L) {
       const bool diag = (I == L);
-      {
-        const int r = tid & (TS - 1), q = tid >> 6;
-#pragma unroll
-        for (int k = 0; k < 16; ++k) As[r + (q * 16 + k) * TLD] = nx[k];
-        if (tid < TS) vL[tid] = vfun(cb + tid);
-        else if (tid < 2 * TS) vI[tid - TS] = vfun(rb + tid - TS);
-      }
-      __syncthreads();
-      if (t + Gt < ntt) {
-        int I2, L2;
-        tile_of(t + Gt, I2, L2);
-        load_tile(I2, L2);
-      }
       {
         const int x = tid & (TS - 1), q = tid >> 6;
         T sd = zero_<T>(), st = zero_<T>();
 #pragma unroll 4
         for (int k = 0; k < 16; ++k) {
           const int y = q * 16 + k;
-          sd += As[x + y * TLD] * vL[y];                       // row x of the tile
-          if (!diag || y > x) st += conj_(As[y + x * TLD]) * vI[y];  // column x, reflected
+          sd += Ab[x + y * TLD] * vl[y];                       // row x of the tile
+          if (!diag || y > x) st += conj_(Ab[y + x * TLD]) * vi[y];  // column x, reflected
         }
         redD[q * TS + x] = sd;
         redT[q * TS + x] = st;
       }
       __syncthreads();
-      // (the next iteration's shared-memory stores touch As, vI and vL only; its reduction
-      // buffers are written after its first barrier, when every thread has left this one)
+      // (the next tile's shared-memory stores touch its stage only; the reduction buffers are
+      // written again after the next tile's first barrier, when every thread has left this one)
       if (tid < TS) {
         T o = redD[tid] + redD[TS + tid] + redD[2 * TS + tid] + redD[3 * TS + tid];
         if (diag) o += redT[tid] + redT[TS + tid] + redT[2 * TS + tid] + redT[3 * TS + tid];
@@ -299,6 +280,59 @@ __global__ void __launch_bounds__(NT, 2) k_td_panel(TdArgs<T> a) {
       } else if (!diag && tid < 2 * TS) {
         const int x = tid - TS;
         a.slots[((long long)L * ntile + I) * TS + x] = redT[x] + redT[TS + x] + redT[2 * TS + x] + redT[3 * TS + x];
+      }
+    };
+    {
+      // this thread's 16 entries of tile (I, L): row r = tid % 64, columns 16 q .. 16 q + 15
+      T nx[16];
+      T nvr = zero_<T>();  // threads < 128: the raw column-j entry behind the next tile's v_L / v_I
+      auto load_tile = [&](int I, int L) {
+        const int r = tid & (TS - 1), q = tid >> 6;
+        const int rb = (t0 + I) * TS, cb = (t0 + L) * TS, row = rb + r;
+        const bool diag = (I == L), rok = row > j && row < n;
+        if (tid < 2 * TS) {
+          const int iv = tid < TS ? cb + tid : rb + tid - TS;
+          nvr = (iv > j + 1 && iv < n) ? ldcg_(&colj[iv]) : zero_<T>();
+        }
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          const int l = q * 16 + k, col = cb + l;
+          T val = zero_<T>();
+          if (rok && col > j && col < n && (!diag || r >= l)) {
+            val = a.A[row + (long long)col * lda];
+            if (diag && r == l) val = from_re<T>(re_(val));
+          }
+          nx[k] = val;
+        }
+      };
+      if (gt >= 0 && gt < ntt) {
+        int I, L;
+        tile_of(gt, I, L);
+        load_tile(I, L);
+      }
+      // the next tile's entries are loaded into registers while this one is multiplied from shared memory
+      for (long long t = gt; gt >= 0 && t < ntt; t += Gt) {
+        int I, L;
+        tile_of(t, I, L);
+        const int rb = (t0 + I) * TS, cb = (t0 + L) * TS;
+        {
+          const int r = tid & (TS - 1), q = tid >> 6;
+#pragma unroll
+          for (int k = 0; k < 16; ++k) As[r + (q * 16 + k) * TLD] = nx[k];
+          if (tid < 2 * TS) {
+            const int iv = tid < TS ? cb + tid : rb + tid - TS;
+            const T v = iv == j + 1 ? one : (iv > j + 1 && iv < n ? scale * nvr : zero_<T>());
+            if (tid < TS) vL[tid] = v;
+            else vI[tid - TS] = v;
+          }
+        }
+        __syncthreads();
+        if (t + Gt < ntt) {
+          int I2, L2;
+          tile_of(t + Gt, I2, L2);
+          load_tile(I2, L2);
+        }
+        tile_products(As, vL, vI, I, L);
       }
     }
     __syncthreads();
@@ -338,7 +372,7 @@ __global__ void __launch_bounds__(NT, 2) k_td_panel(TdArgs<T> a) {
     for (int l = tid; l < 2 * c; l += NT) {
       const int ll = l % c;
       const int off = l < c ? ll : nb + ll;
-      const T s = ssum<T>(0, a.npd, 1, [&](int q) { return ldcg_(&a.dparts[(long long)q * 2 * nb + off]); });
+      const T s = ssum<T, 8>(0, a.npd, 1, [&](int q) { return ldcg_(&a.dparts[(long long)q * 2 * nb + off]); });
       if (l < c) s_vhv[ll] = s;
       else s_whv[ll] = s;
     }
@@ -356,7 +390,7 @@ __global__ void __launch_bounds__(NT, 2) k_td_panel(TdArgs<T> a) {
         if (ok) {
           const int Ri = i / TS - t0, r = i % TS;
           const T* sl = a.slots + (long long)Ri * ntile * TS + r;
-          acc = ssum<T>(lane, ntile, tpr, [&](int X) { return ldcg_(&sl[(long long)X * TS]); });
+          acc = ssum<T, 8>(lane, ntile, tpr, [&](int X) { return ldcg_(&sl[(long long)X * TS]); });
           acc -= ssum<T>(lane, c, tpr, [&](int l) {
             const long long o = i + (long long)l * ldw;
             return ldcg_(&Vp[o]) * s_whv[l] + ldcg_(&Wp[o]) * s_vhv[l];
@@ -428,7 +462,7 @@ __global__ void k_real_to(int n, int k, const double* Z, long long ldz, T* Y, lo
   }
 }
 
-template <class T> size_t td_smem() { return sizeof(T) * ((size_t)TS * TLD + 2 * TS + 8 * TS) + 64; }
+template <class T> size_t td_smem() { return sizeof(T) * ((size_t)STG + 8 * TS) + 64; }
 
 }  // namespace
 
@@ -464,8 +498,8 @@ template <class T> int he2td(Sys& s, T* A, int lda) {
   a.nparts = (double*)pw_base;                       // gmax doubles
   a.aparts = (T*)(pw_base + 2048 * 8);               // gmax values
   a.piv = (T*)(pw_base + 2048 * 8 + 2048 * 16);
-  a.dparts = (T*)(pw_base + 2048 * 8 + 2048 * 16 + 256);  // 16 x 2nb values
-  if ((size_t)2048 * 8 + 2048 * 16 + 256 + (size_t)16 * 2 * nb * sizeof(T) > s.panelws_bytes || gmax > 2048 ||
+  a.dparts = (T*)(pw_base + 2048 * 8 + 2048 * 16 + 256);  // 32 x 2nb values
+  if ((size_t)2048 * 8 + 2048 * 16 + 256 + (size_t)32 * 2 * nb * sizeof(T) > s.panelws_bytes || gmax > 2048 ||
       gmax < 2)
     return GEV_ERR_UNSUPPORTED;
   a.gb = GridBar{(unsigned*)&s.status[ST_BARRIER_CNT], (unsigned*)&s.status[ST_BARRIER_GEN], s.status,
@@ -475,8 +509,8 @@ template <class T> int he2td(Sys& s, T* A, int lda) {
     const int pw = std::min(nb, n - j0);
     const long long nt0 = (long long)((n + TS - 1) / TS - (j0 + 1) / TS);
     const long long ntt = nt0 * (nt0 + 1) / 2;
-    // dot blocks (V^H v, W^H v over ~256 rows each, at most 16) beside the tile blocks
-    const int npd = std::max(1, std::min(16, (n - j0) / 256));
+    // dot blocks (V^H v, W^H v over ~128 rows each, at most 32) beside the tile blocks
+    const int npd = std::max(1, std::min(32, (n - j0) / 128));
     const int G = npd + (int)std::min<long long>(gmax - npd, std::max<long long>(ntt, 1));
     a.j0 = j0;
     a.pw = pw;
