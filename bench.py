@@ -376,6 +376,11 @@ CONFIGS = [  # (name, n, k, seed, complex, cluster)
 ]
 
 
+def one_stage_opt(args):
+    """--one-stage as the Solver's one_stage argument (None = automatic)."""
+    return {"auto": None, "on": True, "off": False}[getattr(args, "one_stage", "auto")]
+
+
 def run_configs(args):
     """The smaller configurations timed on the GPU (plain FP64 with emulated and native products, and
     the mixed form): median of ``--steps`` solves after ``--warmup``, CUDA events on the solve
@@ -471,7 +476,8 @@ def workload_config(args):
                         f"eigenpairs, seed {args.seed}, Toeplitz S, DFT-like spectrum; "
                         f"{'mixed' if args.mixed else 'plain FP64'} path",
             "n": args.n, "k": args.k, "precision": "mixed" if args.mixed else "plain",
-            "band_b": args.band_b, "l2": "inputs (2 x n^2 x 8 B) larger than L2; no flush needed"}
+            "band_b": args.band_b, "tridiag_route": getattr(args, "one_stage", "auto"),
+            "l2": "inputs (2 x n^2 x 8 B) larger than L2; no flush needed"}
 
 
 def main():
@@ -509,6 +515,8 @@ def main():
     ap.add_argument("--stream-only", action="store_true",
                     help="run only the k-point stream (both precisions) and print its line")
     ap.add_argument("--band-b", type=int, default=64)
+    ap.add_argument("--one-stage", default="auto", choices=["auto", "on", "off"],
+                    help="tridiagonalisation route of the headline solve (gev_opts.one_stage)")
     ap.add_argument("--fp32-products", type=int, default=-1, choices=[-1, 0, 3, 6],
                     help="mixed form, FP32 products: 6 / 3 = BF16x6 / BF16x3 on the tensor cores, "
                          "0 = FP32 CUDA cores, -1 = automatic")
@@ -564,7 +572,8 @@ def main():
     stream = torch.cuda.current_stream(dev)
     solver = gev.Solver(args.n, complex_=args.complex, device=dev, mixed=args.mixed,
                         band_b=args.band_b, timing=2, stream=stream, fp64_emulation=args.fp64_emulation,
-                        fp32_products=args.fp32_products, rr_band_b=args.rr_band_b)
+                        fp32_products=args.fp32_products, rr_band_b=args.rr_band_b,
+                        one_stage=one_stage_opt(args))
     w = torch.empty(args.k, dtype=torch.float64, device=dev)
     Cb = torch.empty((args.k, args.n), dtype=solver.dtype, device=dev)
     for _ in range(args.warmup):
@@ -653,7 +662,8 @@ def main():
             plain_emu = time_plain(1, args.plain_steps)
         solver = gev.Solver(args.n, complex_=args.complex, device=dev, mixed=args.mixed,
                             band_b=args.band_b, timing=0, stream=stream, fp64_emulation=args.fp64_emulation,
-                            fp32_products=args.fp32_products, rr_band_b=args.rr_band_b)
+                            fp32_products=args.fp32_products, rr_band_b=args.rr_band_b,
+                        one_stage=one_stage_opt(args))
     # end-to-end through the Python API with pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -682,7 +692,7 @@ def main():
         solver.close()
         cs = gev.Solver(args.n, complex_=args.complex, device=dev, mixed=args.mixed, band_b=args.band_b,
                         stream=stream, fp64_emulation=args.fp64_emulation, fp32_products=args.fp32_products,
-                        check=True, rr_band_b=args.rr_band_b)
+                        check=True, rr_band_b=args.rr_band_b, one_stage=one_stage_opt(args))
         cs.solve_cm(Hb, Sb, args.k, w, Cb)
         accuracy = {"resid": cs.last_report["resid"], "ortho": cs.last_report["ortho"],
                     "bound_resid": 1e-11 if args.mixed else 1e-13 * args.n ** 0.5,
