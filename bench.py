@@ -74,6 +74,11 @@ def steps_roofline(step_ms, n, k, b, complex_, mixed, emulated, refine_iters, fp
         fma = ("FP64 FMA on the CUDA cores", FP64_FMA_TF)
     else:
         fma = ("FP32 (complex64) FMA on the CUDA cores", FP32_FMA_TF)
+    # back-transform 2: compact-WY tensor-core products on the emulated engine, else reflector by
+    # reflector on the FMA pipe; the mixed form back-transforms all N FP32 vectors (the refinement
+    # uses the complement), the plain forms the k wanted ones
+    bt2 = fp64 if (emulated and not mixed) else fma
+    KB = N if mixed else K
     work = {
         "cholesky": (2.0 * N ** 3 / 3.0, fp64),  # Cholesky and inversion, one fused recursion
         "multiply": (N ** 3, fp64),
@@ -81,8 +86,8 @@ def steps_roofline(step_ms, n, k, b, complex_, mixed, emulated, refine_iters, fp
         "to_tridiag": (6.0 * B * N * N, fma),  # bulge chasing: bound by the 3N-task critical path
         "solve": (None, ("secular equations in FP64 on the CUDA cores; merge products on the product engine",
                          None)),
-        "back_tridiag": (2.0 * N * N * K, fma),
-        "back_band": (2.0 * N * N * K, fp32 if low_real else fp64),
+        "back_tridiag": (2.0 * N * N * KB, bt2),
+        "back_band": (2.0 * N * N * KB, fp32 if low_real else fp64),
         "mult": (N * N * K, fp64),
     }
     if mixed:
