@@ -1,4 +1,5 @@
-"""Autotuner of the band width b of the two-stage tridiagonalisation.
+"""Autotuner of the band width b of the two-stage tridiagonalisation (which is also the panel width of
+the one-stage route; each timed solve takes the route ``gev_opts.one_stage = 0`` picks automatically).
 
 The full -> band step gains from a wide band (its products have inner dimension b), the bulge chasing
 and back-transform 2 lose from it (a band -> tridiagonal task costs ~6 b^2 flops on a 3n-task
@@ -106,8 +107,9 @@ def main():
     dev = torch.device("cuda", 0)
     t0 = time.time()
     entries = tune(args.orders, args.reps, dev)
-    table = {"what": "band width b of the two-stage tridiagonalisation, fastest complete solve (k = n/4) "
-                     "of the seeded synthetic pencil, per dtype/precision and order",
+    table = {"what": "band width b of the two-stage tridiagonalisation (panel width of the one-stage route), "
+                     "fastest complete solve (k = n/4, automatic route) of the seeded synthetic pencil, per "
+                     "dtype/precision and order",
              "candidates": list(CANDIDATES), "reps": args.reps, "gpu": torch.cuda.get_device_name(dev),
              "tuning_s": round(time.time() - t0, 1), "entries": entries}
     with open(args.out, "w") as f:
