@@ -1,6 +1,6 @@
-// One-stage Householder tridiagonalisation ("ELPA1", section "Usability and Tutorials": on GPUs the
-// one-stage solver is the faster choice when all, or most, eigenpairs are wanted), and its
-// back-transform Y = Q Z.
+// One-stage Householder tridiagonalisation ("ELPA1", section "Usability and Tutorials", where the
+// one-stage solver is reported as the faster GPU choice when all, or most, eigenpairs are wanted), and
+// its back-transform Y = Q Z.
 //
 //   A = Q T Q^H,  Q = H_0 H_1 ... H_{n-2},  H_j = I - tau_j v_j v_j^H,  v_j = 0 above row j+1,
 //   v_j(j+1) = 1,  H_j^H A(j+1:, j) = (e_j, 0, ..., 0)^T with e_j real.
@@ -114,7 +114,7 @@ __device__ __forceinline__ int rows_tpr(int nrows) {
 template <class T>
 __global__ void __launch_bounds__(NT, 2) k_td_panel(TdArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  T* As = reinterpret_cast<T*>(smraw);  // stage 0: TS x TLD tile, then two TS-entry vectors
+  T* As = reinterpret_cast<T*>(smraw);  // TS x TLD tile, then the two TS-entry v segments
   T* vI = As + TS * TLD;
   T* vL = vI + TS;
   T* redD = As + STG;  // 4 x TS
@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(NT, 2) k_td_panel(TdArgs<T> a) {
       L = (int)(t - (long long)I * (I + 1) / 2);
     };
     const int gt = g - a.npd, Gt = G - a.npd;  // tile blocks: g >= npd
-    // the tile's products from shared memory (stage base Ab, v_L / v_I in vl / vi); partial sums to
+    // the tile's products from shared memory (tile Ab, v_L / v_I in vl / vi); partial sums to
     // the two slots
     auto tile_products = [&](const T* Ab, const T* vl, const T* vi, int I, int L) {
       const bool diag = (I == L);
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(NT, 2) k_td_panel(TdArgs<T> a) {
         redT[q * TS + x] = st;
       }
       __syncthreads();
-      // (the next tile's shared-memory stores touch its stage only; the reduction buffers are
+      // (the next tile's shared-memory stores touch Ab, vl and vi only; the reduction buffers are
       // written again after the next tile's first barrier, when every thread has left this one)
       if (tid < TS) {
         T o = redD[tid] + redD[TS + tid] + redD[2 * TS + tid] + redD[3 * TS + tid];
