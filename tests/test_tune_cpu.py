@@ -21,3 +21,16 @@ def test_candidates_fit_the_bulge_kernel():
     for b in tune.CANDIDATES:
         assert 3 * b * (b + 1) * 16 <= 227 * 1024
     assert 3 * 128 * 129 * 8 > 227 * 1024  # why 128 is not a candidate
+
+
+def test_committed_table_is_well_formed():
+    """The table shipped with the package: every form, entries from the candidates, the fastest time's b."""
+    table = tune.load(tune.TABLE)
+    assert set(table["entries"]) == {"f64/plain", "f64/mixed", "c128/plain", "c128/mixed"}
+    for form, orders in table["entries"].items():
+        for order, ent in orders.items():
+            assert ent["b"] in tune.CANDIDATES
+            times = {int(b): t for b, t in ent["ms"].items()}
+            assert min(times, key=times.get) == ent["b"], (form, order)
+            cx, mixed = form.startswith("c128"), form.endswith("mixed")
+            assert tune.pick_band(int(order), cx, mixed, table) == ent["b"]
