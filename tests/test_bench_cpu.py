@@ -47,6 +47,13 @@ def test_steps_roofline_counts():
     rm = bench.steps_roofline(fake_ms(1000.0), n, k, b, False, True, True, 3, 6, MP)
     assert math.isclose(rm["refine"]["tflops"], 3 * (2 * n * n * k + 3 * n * k * k) / 1e12)
     assert math.isclose(rm["to_band"]["peak_tflops"], 1764.7 / 6)
+    # the mixed form back-transforms all n FP32 vectors; the plain emulated form's back-transform 2 runs on
+    # the tensor-core product engine, the native one on the FP64 FMA pipe
+    assert math.isclose(rm["back_tridiag"]["tflops"], 2 * n ** 3 / 1e12)
+    assert math.isclose(rm["back_band"]["tflops"], 2 * n ** 3 / 1e12)
+    assert math.isclose(r["back_tridiag"]["peak_tflops"], 1764.7 / 36)
+    rn = bench.steps_roofline(fake_ms(1000.0), n, k, b, False, False, False, 0, -1, MP)
+    assert "FMA" in rn["back_tridiag"]["engine"]
 
 
 def test_steps_roofline_zero_time_has_no_rate():
